@@ -1,0 +1,381 @@
+"""Benchmark of the GB300 stable MSD radix sorter (one JSON line on rank 0).
+
+A "step" sorts one batch of synthetic records end to end through the C ABI
+(histograms, distribution passes, on-chip bin sorts).  The default workload
+is 2^31 records of 16 bytes (uniform u64 key + u64 index payload).  Before
+each timed step the input is restored from a pristine device copy (untimed);
+the 32 GiB input is far larger than the 129 MB L2, so no step starts warm.
+
+Reported next to records/s:
+  * roofline -- the dominant kernel (the distribution pass): algorithmic bytes
+    per launch (read + write of every record it moves) over its launch time
+    measured live with CUDA events recorded by the library on the launching
+    stream, against the measured HBM copy bandwidth;
+  * cpu_baseline -- the CPU oracle (LSD counting sort) on a bounded sample of
+    the same workload on this host's cores;
+  * e2e -- the same metric with the records in pinned host memory, the
+    host->device copy, the sort and the device->host copy of the sorted
+    records all inside the timed region.
+
+``--impl reference`` times the CPU oracle instead (the only reference there
+is for this method) on bounded samples of the same workload.
+Multi-GPU (torchrun): every rank sorts its own array (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+METRIC = "sorted records/s and % HBM peak at 1 GB300; plain vs learned/batched, bit-exact"
+UNIT = "records/s"
+
+WORKLOADS = {
+    "uniform16": dict(desc="2^31 records x 16 B (u64 key uniform over 2^64 + u64 index payload), plain MSD sort",
+                      n=1 << 31, rec=16, key=8),
+    "uniform8": dict(desc="2^20 records x 8 B (u64 key only, uniform), plain MSD sort", n=1 << 20, rec=8, key=8),
+    "skewed16": dict(desc="2^30 records x 16 B, Zipf(1.1)/exponential/normal key mixture, plain MSD sort",
+                     n=1 << 30, rec=16, key=8),
+    "widekey32": dict(desc="2^28 records x 32 B, 16-byte key (Zipf(1.0) high word, uniform low word)",
+                      n=1 << 28, rec=32, key=16),
+}
+
+# ncu DRAM traffic of one distribution launch, per record moved, measured on
+# the uniform 16-byte workload (profiles/scatter_uniform16.md); None until taken
+# for the current kernel.
+SCATTER_DRAM_BYTES_PER_RECORD = None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_input(name: str, n: int):
+    """Pinned host records of the workload (uint64, (n, rec/8))."""
+    import torch
+    w = WORKLOADS[name]
+    rw = w["rec"] // 8
+    host = torch.empty((n, rw), dtype=torch.int64, pin_memory=True)
+    arr = host.numpy().view(np.uint64)
+    gen = getattr(datagen, name)
+    if name == "uniform8":
+        arr[:] = gen(n)
+    else:
+        gen(n, out=arr)
+    return host
+
+
+def cpu_baseline(name: str, budget_s: float = 15.0) -> dict:
+    """The oracle, as it stands, on a bounded prefix of the workload."""
+    import oracle
+    w = WORKLOADS[name]
+    cores = oracle.usable_cores()
+    m = 1 << 22
+    gen = getattr(datagen, name)
+    recs = gen(m) if name == "uniform8" else gen(m)
+    t0 = time.perf_counter()
+    oracle.sort(recs, w["key"], threads=cores)
+    dt = time.perf_counter() - t0
+    target = int(m * budget_s / max(dt, 1e-3))
+    m2 = max(m, min(1 << 28, w["n"], 1 << int(np.log2(max(target, 1)))))
+    if m2 > m:
+        recs = gen(m2)
+        t0 = time.perf_counter()
+        oracle.sort(recs, w["key"], threads=cores)
+        dt = time.perf_counter() - t0
+        m = m2
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {m} records of the {name} workload ({w['rec']} B records), one LSD oracle sort "
+                      f"with {cores} threads, {dt:.2f} s"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """--impl reference: the CPU oracle timed on bounded samples of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    w = WORKLOADS[args.workload]
+    cores = oracle.usable_cores()
+    gen = getattr(datagen, args.workload)
+    m = args.ref_records or (1 << 24)
+    recs = gen(m)
+    for _ in range(args.warmup):
+        oracle.sort(recs, w["key"], threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sort(recs, w["key"], threads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = m * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "n_records": m, "rec_bytes": w["rec"],
+                   "key_bytes": w["key"], "sample": "bounded prefix of the workload, sorted on the host"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {m} records of {args.workload}, LSD oracle, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def check_sorted_gpu(recs, pristine_keys=None) -> bool:
+    """Order + stability check on the device (payload = input index)."""
+    import torch
+    k = recs[:, 0] ^ (-(1 << 63))
+    ok = bool(((k[1:] > k[:-1]) | ((k[1:] == k[:-1]) & (recs[1:, 1] > recs[:-1, 1]))).all())
+    if pristine_keys is not None:
+        ok = ok and bool((pristine_keys[recs[:, 1]] == recs[:, 0]).all())
+    return ok
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform16", choices=sorted(WORKLOADS))
+    ap.add_argument("--records", type=int, default=0, help="override the workload's record count")
+    ap.add_argument("--ref-records", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    # the CPU baseline runs before any GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_budget_s)
+
+    import torch
+    import paper_1612_02557_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build_library()
+    pkg.load()
+
+    w = WORKLOADS[args.workload]
+    n = args.records or w["n"]
+    rec, key = w["rec"], w["key"]
+    rw = rec // 8
+
+    host_in = make_input(args.workload, n)
+    pristine = host_in.to("cuda", non_blocking=False)
+    recs = torch.empty_like(pristine)
+    tmp = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (untimed), first one checked
+    for i in range(args.warmup):
+        recs.copy_(pristine)
+        pkg.raduls_sort(recs, tmp, n, rec, key)
+        if i == 0:
+            torch.cuda.synchronize()
+            st = pkg.raduls_stream_status()
+            if st != 0:
+                raise SystemExit(f"device status {st} during warm-up")
+            if rec >= 16 and key == 8:
+                assert check_sorted_gpu(recs, pristine[:, 0]), "warm-up sort output is not the stable order"
+
+    hbm_peak, peak_kind = peaks()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms = []
+    scat_ms = scat_launches = 0.0
+    scat_bytes = 0
+    launches = 0
+    total_bytes = 0
+    kernel_ms = {}
+    for _ in range(args.steps):
+        recs.copy_(pristine)                      # restore the input (untimed)
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode="plain", stats=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        step_ms.append(ev0.elapsed_time(ev1))
+        scat_ms += st["kernel_ms"]["scatter"]
+        scat_launches += st["kernel_launches"]["scatter"]
+        scat_bytes += st["scatter_bytes"]
+        launches += st["gpu_launches"]
+        total_bytes += st["hist_bytes_read"] + st["scatter_bytes"] + st["block_bytes"]
+        for k, v in st["kernel_ms"].items():
+            kernel_ms[k] = kernel_ms.get(k, 0.0) + v
+    clocks = sampler.stop()
+    if pkg.raduls_stream_status() != 0:
+        raise SystemExit("device-side error during the timed steps")
+
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = n * world * args.steps / (tot_ms / 1e3)
+
+    # end to end: pinned host records -> device -> sort -> device -> pinned host
+    e2e = None
+    if args.e2e_steps > 0:
+        host_out = torch.empty_like(host_in, pin_memory=True)
+        e2e_ms = []
+        for _ in range(args.e2e_steps):
+            barrier()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            recs.copy_(host_in, non_blocking=True)
+            pkg.raduls_sort(recs, tmp, n, rec, key)
+            host_out.copy_(recs, non_blocking=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            e2e_ms.append(ev0.elapsed_time(ev1))
+        et = sum(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([et], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": n * world * args.e2e_steps / (et / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": n * rec, "d2h_bytes_per_step": n * rec,
+               "ms_per_step": et / args.e2e_steps}
+        del host_out
+
+    achieved = (scat_bytes / (scat_ms / 1e3)) / 1e9 if scat_ms > 0 else None
+    traffic = None
+    if SCATTER_DRAM_BYTES_PER_RECORD is not None and scat_launches:
+        traffic = SCATTER_DRAM_BYTES_PER_RECORD * (scat_bytes / (2 * rec)) / scat_launches
+    roofline = {
+        "bound": "hbm", "kernel": "scatter_kernel (MSD distribution pass)",
+        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": (achieved / hbm_peak) if achieved else None,
+        "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+        "algorithmic_bytes_per_launch": scat_bytes / max(scat_launches, 1),
+        "launch_ms_avg": scat_ms / max(scat_launches, 1),
+        "whole_sort_gbs": total_bytes / (tot_ms / 1e3) / 1e9 / world if tot_ms else None,
+        "whole_sort_frac": (total_bytes / (tot_ms / 1e3) / 1e9 / world) / hbm_peak if tot_ms else None,
+        "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items() if v > 0},
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "n_records": n, "rec_bytes": rec,
+                   "key_bytes": key, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "input 32 GiB-class, far larger than L2; restored from a pristine device copy before each step"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

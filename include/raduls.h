@@ -1,0 +1,154 @@
+/*
+ * raduls.h -- C ABI of the GB300 (sm_103a) stable MSD radix sorter of
+ * fixed-size records ("RADULS", Kokot, Deorowicz, Debudaj-Grabysz,
+ * arXiv:1612.02557).
+ *
+ * Problem (Sec. 4 of the paper: records of 8..32 bytes whose first 8 or 16
+ * bytes are the key; Sec. 1: radix sort by digits of the key): sort n records
+ * of rec_bytes bytes by a key made of the first key_bytes bytes.  The key is
+ * read as key_bytes/8 little-endian u64 words, word 0 most significant,
+ * compared as unsigned integers lexicographically.  The sort is STABLE:
+ * records with equal keys keep their input order, so the output is unique and
+ * is moved bit for bit.
+ *
+ * Method (Sec. 3.1-3.4): MSD radix sort with radix 256.  Each pass over a bin
+ * builds a digit histogram, turns it into bin offsets with an exclusive prefix
+ * (Sec. 1), and distributes whole records stably; big bins recurse with more
+ * passes (Sec. 3.3), small bins are finished by an on-chip sort (Sec. 3.4,
+ * 3.5).  Digits that are constant within a bin are skipped without moving data.
+ *
+ * Conventions for every call below:
+ *  - Pointers named d_* and the record buffers `in`/`tmp` are DEVICE pointers
+ *    on the current CUDA device.  The caller owns them.  `in` and `tmp` must be
+ *    16-byte aligned, must not overlap, and each must hold n_recs*rec_bytes
+ *    bytes.  The sorted records end up in `in`; `tmp` is scratch whose
+ *    contents afterwards are undefined.
+ *  - rec_bytes % 8 == 0, key_bytes % 8 == 0, 8 <= key_bytes <= rec_bytes <= 256,
+ *    and n_recs*rec_bytes must not overflow 64 bits.  n_recs <= 1 is a no-op.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream).  Argument errors are returned at once and nothing is enqueued.
+ *    The library keeps a per-device workspace (allocated on first use, grown
+ *    when a larger problem arrives) and may synchronise `stream` between
+ *    passes to plan the next one.
+ *  - Errors detected on the device (a bounded wait that ran out) are recorded
+ *    in a per-device status word and returned by raduls_stream_status().  No
+ *    call traps or aborts the CUDA context.
+ *  - Calls from several host threads are serialised internally per device.
+ */
+#ifndef RADULS_H
+#define RADULS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RADULS_OK = 0,
+    RADULS_ERR_INVALID_ARG = 1,  /* bad size, key/record shape or NULL pointer */
+    RADULS_ERR_MISALIGNED = 2,   /* in/tmp not 16-byte aligned, or overlapping */
+    RADULS_ERR_UNSUPPORTED = 3,  /* rec_bytes > 256 or a mode this build lacks */
+    RADULS_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    RADULS_ERR_OOM = 5,          /* the workspace could not be allocated */
+    RADULS_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out */
+    RADULS_ERR_INTERNAL = 7      /* an internal capacity check failed on the device */
+} raduls_status;
+
+/* Sort n_recs records of rec_bytes bytes in `in` by their first key_bytes
+ * bytes (stable, ascending).  See the conventions above. */
+int raduls_sort(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                void *stream);
+
+/* Kernel classes of raduls_stats.kernel_ms / kernel_launches. */
+enum {
+    RADULS_K_SETUP = 0,     /* work-list set-up and per-level resets */
+    RADULS_K_HIST = 1,      /* digit histograms of big bins (first traversal, Sec. 1) */
+    RADULS_K_PLAN = 2,      /* prefix sums and sub-bin classification (Fig. 1-3 on the GPU) */
+    RADULS_K_SCATTER = 3,   /* stable distribution of big bins (second traversal, Sec. 1) */
+    RADULS_K_COPY = 4,      /* copy-back of finished bins left in tmp */
+    RADULS_K_BLOCK = 5,     /* on-chip sorts of small-bin runs (Sec. 3.4-3.5) */
+    RADULS_K_LEARNED = 6,   /* learned-partition fit, count and distribution */
+    RADULS_K_BATCHED = 7,   /* persistent batched segmented sort */
+    RADULS_K_COUNT = 8
+};
+
+/* Statistics of one sort, filled when the call returns (the call synchronises
+ * its stream when a stats pointer is given). */
+typedef struct {
+    uint32_t grid_passes;        /* device-wide distribution passes run (Sec. 3.2-3.3) */
+    uint32_t levels;             /* MSD levels planned */
+    uint64_t hist_bytes_read;    /* algorithmic bytes read by histogram passes */
+    uint64_t scatter_bytes;      /* algorithmic bytes read + written by distribution passes */
+    uint64_t block_bytes;        /* bytes read + written by on-chip bin sorts and copies */
+    uint64_t block_items;        /* on-chip sort items (packed runs of small bins) */
+    uint64_t skipped_digits;     /* bin-digits skipped because they were constant */
+    uint32_t learned_used;       /* 1 when the learned first partition ran */
+    uint32_t learned_fell_back;  /* 1 when the learned partition was rejected */
+    float    learned_ratio;      /* max bucket / ideal bucket size of the learned model */
+    uint32_t gpu_launches;       /* kernels this call launched */
+    /* Device time per kernel class, measured with CUDA events recorded on the
+     * call's stream around each launch, and launches per class, indexed by
+     * the RADULS_K_* classes above. */
+    float    kernel_ms[RADULS_K_COUNT];
+    uint32_t kernel_launches[RADULS_K_COUNT];
+} raduls_stats;
+
+typedef struct {
+    uint32_t mode;                  /* 0 AUTO, 1 PLAIN, 2 LEARNED */
+    uint32_t learned_log2_buckets;  /* 12..16, 0 = default */
+    float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio; 0 = 4.0 */
+    uint32_t use_tuned;             /* 1 = use the tuned launch parameters */
+    raduls_stats *stats;            /* host pointer or NULL */
+} raduls_opts;
+
+/* raduls_sort with options (mode, statistics).  opts may be NULL. */
+int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                   const raduls_opts *opts, void *stream);
+
+/* Sort n_segs independent arrays in one call.  Array s occupies records
+ * [d_seg_offsets[s], d_seg_offsets[s+1]) of `in` (d_seg_offsets is a DEVICE
+ * array of n_segs+1 non-decreasing u64 record offsets with d_seg_offsets[0]
+ * == 0); records never move between arrays.  `tmp` must hold
+ * d_seg_offsets[n_segs] records.  Offsets are checked on the device; a bad
+ * offset table is reported through raduls_stream_status(). */
+int raduls_sort_batched(void *in, void *tmp, const uint64_t *d_seg_offsets, uint32_t n_segs,
+                        uint32_t rec_bytes, uint32_t key_bytes, void *stream);
+
+/* Synchronise `stream`, then return and clear the device-side status of the
+ * current device (RADULS_OK if no device-side error was recorded). */
+int raduls_stream_status(void *stream);
+
+/* Static text for a status code. */
+const char *raduls_status_string(int status);
+
+/* ---- single-step entry points (one kernel each; used to test each step) ---- */
+
+/* Histogram of digit `digit` (0 = least significant key byte; byte digit%8 of
+ * key word key_bytes/8-1-digit/8) over all n_recs records: d_hist_out[256] u64
+ * (device).  First traversal of a counting pass (Sec. 1). */
+int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                     uint32_t digit, uint64_t *d_hist_out, void *stream);
+
+/* One stable distribution pass on digit `digit` over the whole array, `in` ->
+ * `out` (device, n_recs*rec_bytes each, not overlapping): the histogram, the
+ * exclusive prefix and the stable scatter of Sec. 1 done by the GPU pass
+ * kernels (tile ranking + single-pass look-back scan). */
+int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_t rec_bytes,
+                             uint32_t key_bytes, uint32_t digit, void *stream);
+
+/* Test hook: make the next distribution pass withhold tile `tile`'s published
+ * counts so that its successors' bounded waits run out (kind 1), or clear the
+ * hook (kind 0).  The pass then reports RADULS_ERR_TIMEOUT through
+ * raduls_stream_status() and skips its writes; the context stays usable. */
+int raduls_debug_inject(uint32_t kind, uint64_t tile);
+
+/* Device-side wait limit in nanoseconds for look-back spins (default 2e9). */
+int raduls_set_wait_limit_ns(uint64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADULS_H */

@@ -1,0 +1,219 @@
+"""ctypes binding of ``libraduls.so`` (argument marshalling only).
+
+Buffers may be given as torch CUDA tensors (any dtype; their bytes are the
+records) or as raw integer device addresses.  ``stream`` may be a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None for the
+current torch stream of the tensors' device (the legacy default stream when
+no tensor is given).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+STATUS = {
+    0: "RADULS_OK",
+    1: "RADULS_ERR_INVALID_ARG",
+    2: "RADULS_ERR_MISALIGNED",
+    3: "RADULS_ERR_UNSUPPORTED",
+    4: "RADULS_ERR_CUDA",
+    5: "RADULS_ERR_OOM",
+    6: "RADULS_ERR_TIMEOUT",
+    7: "RADULS_ERR_INTERNAL",
+}
+
+
+class RaduLSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where} failed: {STATUS.get(code, code)}")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("grid_passes", ctypes.c_uint32),
+        ("levels", ctypes.c_uint32),
+        ("hist_bytes_read", ctypes.c_uint64),
+        ("scatter_bytes", ctypes.c_uint64),
+        ("block_bytes", ctypes.c_uint64),
+        ("block_items", ctypes.c_uint64),
+        ("skipped_digits", ctypes.c_uint64),
+        ("learned_used", ctypes.c_uint32),
+        ("learned_fell_back", ctypes.c_uint32),
+        ("learned_ratio", ctypes.c_float),
+        ("gpu_launches", ctypes.c_uint32),
+        ("kernel_ms", ctypes.c_float * 8),
+        ("kernel_launches", ctypes.c_uint32 * 8),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "kernel_launches")}
+        d["kernel_ms"] = {KERNEL_CLASSES[i]: float(self.kernel_ms[i]) for i in range(8)}
+        d["kernel_launches"] = {KERNEL_CLASSES[i]: int(self.kernel_launches[i]) for i in range(8)}
+        return d
+
+
+KERNEL_CLASSES = ["setup", "hist", "plan", "scatter", "copy", "block", "learned", "batched"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_uint32),
+        ("learned_log2_buckets", ctypes.c_uint32),
+        ("fallback_ratio", ctypes.c_float),
+        ("use_tuned", ctypes.c_uint32),
+        ("stats", ctypes.POINTER(Stats)),
+    ]
+
+
+MODES = {"auto": 0, "plain": 1, "learned": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    return _build.build(force=force, verbose=verbose)
+
+
+def load():
+    """Load libraduls.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1612_02557_gb300.build_library() "
+                               "(the sorter has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+        sigs = {
+            "raduls_sort": [vp, vp, u64, u32, u32, vp],
+            "raduls_sort_ex": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
+            "raduls_sort_batched": [vp, vp, vp, u32, u32, u32, vp],
+            "raduls_histogram": [vp, u64, u32, u32, u32, vp, vp],
+            "raduls_distribution_pass": [vp, vp, u64, u32, u32, u32, vp],
+            "raduls_stream_status": [vp],
+            "raduls_debug_inject": [u32, u64],
+            "raduls_set_wait_limit_ns": [u64],
+        }
+        for name, args in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.raduls_status_string.argtypes = [ctypes.c_int]
+        lib.raduls_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    dp = getattr(x, "data_ptr", None)
+    if dp is None:
+        raise TypeError(f"expected a CUDA tensor or a device address, got {type(x)}")
+    if not x.is_cuda:
+        raise ValueError("buffers must live on a CUDA device")
+    if not x.is_contiguous():
+        raise ValueError("buffers must be contiguous")
+    return int(dp())
+
+
+def _nbytes(x) -> int | None:
+    if isinstance(x, int) or x is None:
+        return None
+    return x.numel() * x.element_size()
+
+
+def _stream(stream, *tensors) -> int:
+    if stream is None:
+        for t in tensors:
+            if t is not None and not isinstance(t, int):
+                import torch
+                return int(torch.cuda.current_stream(t.device).cuda_stream)
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _check_size(x, need: int, name: str):
+    nb = _nbytes(x)
+    if nb is not None and nb < need:
+        raise ValueError(f"{name} holds {nb} bytes, needs {need}")
+
+
+def _raise(rc: int, where: str):
+    if rc != 0:
+        raise RaduLSError(rc, where)
+
+
+def raduls_sort(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, stream=None) -> None:
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(tmp, n_recs * rec_bytes, "tmp")
+    rc = load().raduls_sort(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes, _stream(stream, in_, tmp))
+    _raise(rc, "raduls_sort")
+
+
+def raduls_sort_ex(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, mode: str = "auto",
+                   learned_log2_buckets: int = 0, fallback_ratio: float = 0.0, use_tuned: bool = True,
+                   stats: bool = False, stream=None) -> dict | None:
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(tmp, n_recs * rec_bytes, "tmp")
+    st = Stats()
+    o = Opts(MODES[mode], learned_log2_buckets, fallback_ratio, 1 if use_tuned else 0,
+             ctypes.pointer(st) if stats else None)
+    rc = load().raduls_sort_ex(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes, ctypes.byref(o),
+                               _stream(stream, in_, tmp))
+    _raise(rc, "raduls_sort_ex")
+    return st.as_dict() if stats else None
+
+
+def raduls_sort_batched(in_, tmp, seg_offsets, n_segs: int, rec_bytes: int, key_bytes: int, stream=None) -> None:
+    rc = load().raduls_sort_batched(_addr(in_), _addr(tmp), _addr(seg_offsets), n_segs, rec_bytes, key_bytes,
+                                    _stream(stream, in_, tmp))
+    _raise(rc, "raduls_sort_batched")
+
+
+def raduls_histogram(in_, n_recs: int, rec_bytes: int, key_bytes: int, digit: int, hist_out, stream=None) -> None:
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(hist_out, 256 * 8, "hist_out")
+    rc = load().raduls_histogram(_addr(in_), n_recs, rec_bytes, key_bytes, digit, _addr(hist_out),
+                                 _stream(stream, in_))
+    _raise(rc, "raduls_histogram")
+
+
+def raduls_distribution_pass(in_, out, n_recs: int, rec_bytes: int, key_bytes: int, digit: int,
+                             stream=None) -> None:
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(out, n_recs * rec_bytes, "out")
+    rc = load().raduls_distribution_pass(_addr(in_), _addr(out), n_recs, rec_bytes, key_bytes, digit,
+                                         _stream(stream, in_, out))
+    _raise(rc, "raduls_distribution_pass")
+
+
+def raduls_stream_status(stream=None) -> int:
+    return int(load().raduls_stream_status(_stream(stream)))
+
+
+def raduls_status_string(code: int) -> str:
+    return load().raduls_status_string(code).decode()
+
+
+def raduls_debug_inject(kind: int, tile: int = 0) -> None:
+    _raise(load().raduls_debug_inject(kind, tile), "raduls_debug_inject")
+
+
+def raduls_set_wait_limit_ns(ns: int) -> None:
+    _raise(load().raduls_set_wait_limit_ns(ns), "raduls_set_wait_limit_ns")

@@ -1,0 +1,329 @@
+// plan.cu -- device-side planning of the MSD recursion.
+//
+// After the histogram of every big bin is known, plan_kernel does on the GPU
+// what the paper's scheduler does on the CPU (Fig. 1-3, Sec. 3.2-3.4): it
+// turns each histogram into sub-bin offsets (exclusive prefix, Sec. 1), and
+// sends every sub-bin where it belongs:
+//   * still bigger than one CTA can sort on chip -> next device-wide pass on
+//     the next digit (the "big bins" of Sec. 3.3, Fig. 2);
+//   * small -> packed with its small neighbours into runs of at most cap_b
+//     records that one CTA sorts on chip (the "small"/"tiny" bins of Sec. 3.4
+//     and 3.5, Fig. 3);
+//   * no digits left but still in the scratch buffer -> copied back.
+// A bin whose digit is the same for all its records is not distributed: it
+// moves on to its next varying digit without any data movement.
+#include "kernels.h"
+
+namespace raduls {
+
+__device__ __forceinline__ u32 ceil_div_u64(u64 a, u32 b) { return (u32)((a + b - 1) / b); }
+
+// Append a bin to the next grid list and map its histogram tiles.
+__device__ void append_grid(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+{
+    const u32 slot = atomicAdd(&a.ctrs->grid_next, 1u);
+    const u32 nt = ceil_div_u64(count, a.tile_h);
+    const u32 tb = atomicAdd(&a.ctrs->grid_next_tiles, nt);
+    if (slot >= a.caps.grid || (u64)tb + nt > a.caps.hist_tiles) {
+        set_error(a.ctrs, ST_INTERNAL);
+        return;
+    }
+    WorkItem it;
+    it.begin = begin;
+    it.count = count;
+    it.digit = digit;
+    it.flags = flags;
+    it.tile_base = tb;
+    it.row = slot;
+    a.grid_next[slot] = it;
+    for (u32 j = 0; j < nt; ++j)
+        a.tile_hist[tb + j] = slot;
+}
+
+__device__ void append_copy(const PlanArgs &a, u64 begin, u64 count)
+{
+    const u32 slot = atomicAdd(&a.ctrs->copy, 1u);
+    const u32 nt = ceil_div_u64(count, a.tile_c);
+    const u32 tb = atomicAdd(&a.ctrs->copy_tiles, nt);
+    if (slot >= a.caps.copy || (u64)tb + nt > a.caps.copy_tiles) {
+        set_error(a.ctrs, ST_INTERNAL);
+        return;
+    }
+    WorkItem it;
+    it.begin = begin;
+    it.count = count;
+    it.digit = 0;
+    it.flags = ITEM_IN_TMP;
+    it.tile_base = tb;
+    it.row = slot;
+    a.copies[slot] = it;
+    for (u32 j = 0; j < nt; ++j)
+        a.tile_copy[tb + j] = slot;
+}
+
+__device__ void append_block(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+{
+    const u64 slot = atomicAdd(&a.ctrs->block, 1ull);
+    if (slot >= a.caps.block || count > a.cap_b) {
+        set_error(a.ctrs, ST_INTERNAL);
+        return;
+    }
+    WorkItem it;
+    it.begin = begin;
+    it.count = count;
+    it.digit = digit;
+    it.flags = flags;
+    it.tile_base = 0;
+    it.row = 0;
+    a.blocks[slot] = it;
+}
+
+// Next digit below p that varies inside the bin, judged from the OR and AND of
+// the key word holding p (bytes where they differ vary).  Returns -1 when no
+// digit is left.  When the rest of this word is constant, the top digit of the
+// next word is returned: its own histogram will tell.
+__device__ int next_varying_digit(u32 p, u64 vor, u64 vand)
+{
+    const u64 diff = vor ^ vand;
+    for (int b = (int)(p % 8u) - 1; b >= 0; --b)
+        if ((diff >> (8 * b)) & 0xffu)
+            return (int)(p - (p % 8u)) + b;
+    if (p < 8u)
+        return -1;
+    return (int)(p - (p % 8u)) - 1;
+}
+
+__global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
+{
+    __shared__ u64 s_cnt[RADIX];
+    __shared__ u64 s_ex[RADIX];
+    __shared__ unsigned char s_big[RADIX];
+    __shared__ u64 s_wsum[RADIX / 32];
+    __shared__ u32 s_slot, s_tb, s_nt;
+    const u32 d = threadIdx.x, lane = d & 31u, w = d >> 5;
+    const u32 n_grid = a.ctrs->grid_cur;
+    for (u32 g = blockIdx.x; g < n_grid; g += gridDim.x) {
+        const WorkItem it = a.grid_cur[g];
+        const u32 p = it.digit;
+        const u64 h = a.hist[(u64)g * RADIX + d];
+        const int is_const = __syncthreads_or(h == it.count);
+        if (is_const && !a.single_pass) {
+            if (d == 0) {
+                const int np = next_varying_digit(p, a.orand[2ull * g], a.orand[2ull * g + 1]);
+                if (np >= 0) {
+                    atomicAdd(&a.ctrs->skipped, (u64)(p - (u32)np));
+                    append_grid(a, it.begin, it.count, (u32)np, it.flags);
+                } else {
+                    atomicAdd(&a.ctrs->skipped, (u64)(p + 1));
+                    if (it.flags & ITEM_IN_TMP)
+                        append_copy(a, it.begin, it.count);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // this bin is distributed on digit p in this level's pass
+        if (d == 0) {
+            const u32 slot = atomicAdd(&a.ctrs->scatter, 1u);
+            const u32 nt = ceil_div_u64(it.count, a.tile_s);
+            const u32 tb = atomicAdd(&a.ctrs->scatter_tiles, nt);
+            if (slot >= a.caps.grid || (u64)tb + nt > a.caps.scat_tiles) {
+                set_error(a.ctrs, ST_INTERNAL);
+                s_nt = 0;
+            } else {
+                WorkItem sc = it;
+                sc.tile_base = tb;
+                sc.row = g;
+                a.scat[slot] = sc;
+                s_nt = nt;
+            }
+            s_slot = slot;
+            s_tb = tb;
+        }
+        // exclusive prefix of the histogram: the start of every sub-bin (Sec. 1)
+        u64 incl = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 v = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= (u32)o)
+                incl += v;
+        }
+        if (lane == 31)
+            s_wsum[w] = incl;
+        __syncthreads();
+        u64 add = 0;
+        for (u32 i = 0; i < w; ++i)
+            add += s_wsum[i];
+        const u64 ex = add + incl - h;
+        a.hist[(u64)g * RADIX + d] = it.begin + ex;  // row becomes the digit bases
+        s_cnt[d] = h;
+        s_ex[d] = it.begin + ex;
+        __syncthreads();
+        for (u32 j = d; j < s_nt; j += RADIX)
+            a.tile_scat[s_tb + j] = s_slot;
+        if (a.single_pass) {
+            __syncthreads();
+            continue;
+        }
+        const u32 cflags = it.flags ^ ITEM_IN_TMP;
+        const bool big = h > a.cap_b;
+        s_big[d] = big ? 1 : 0;
+        if (big) {
+            if (p > 0)
+                append_grid(a, it.begin + ex, h, p - 1, cflags);
+            else if (cflags & ITEM_IN_TMP)
+                append_copy(a, it.begin + ex, h);
+        }
+        __syncthreads();
+        if (d == 0) {
+            // pack consecutive small sub-bins into runs of at most cap_b records
+            u64 acc_b = 0, acc_n = 0;
+            for (u32 c = 0; c < RADIX; ++c) {
+                const u64 n = s_cnt[c];
+                if (s_big[c]) {
+                    if (acc_n)
+                        append_block(a, acc_b, acc_n, p, cflags);
+                    acc_n = 0;
+                    continue;
+                }
+                if (n == 0)
+                    continue;
+                if (acc_n && acc_n + n > a.cap_b) {
+                    append_block(a, acc_b, acc_n, p, cflags);
+                    acc_n = 0;
+                }
+                if (acc_n == 0)
+                    acc_b = s_ex[c];
+                acc_n += n;
+            }
+            if (acc_n)
+                append_block(a, acc_b, acc_n, p, cflags);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top,
+                            u32 cap_b, u32 tile_h, u32 force_grid)
+{
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool grid = force_grid || n > cap_b;
+    const u32 nt = grid ? (u32)((n + tile_h - 1) / tile_h) : 0u;
+    if (i == 0) {
+        Counters c = {};
+        if (grid) {
+            WorkItem it = {0ull, n, top, 0u, 0u, 0u};
+            grid0[0] = it;
+            c.grid_cur = 1;
+            c.grid_cur_tiles = nt;
+        } else if (n > 1) {
+            WorkItem it = {0ull, n, top, 0u, 0u, 0u};
+            blocks[0] = it;
+            c.block = 1;
+        }
+        *ctrs = c;
+    }
+    for (u64 j = i; j < nt; j += (u64)gridDim.x * blockDim.x)
+        tile_hist[j] = 0;
+}
+
+__global__ void prep_kernel(u64 *hist, u64 *orand, const Counters *ctrs)
+{
+    const u64 rows = ctrs->grid_cur;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows * RADIX; i += stride)
+        hist[i] = 0;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
+        orand[2 * i] = 0;
+        orand[2 * i + 1] = ~0ull;
+    }
+}
+
+__global__ void advance_kernel(Counters *c)
+{
+    c->levels += 1;
+    if (c->scatter)
+        c->grid_passes += 1;
+    c->grid_cur = c->grid_next;
+    c->grid_cur_tiles = c->grid_next_tiles;
+    c->grid_next = 0;
+    c->grid_next_tiles = 0;
+    c->scatter = 0;
+    c->scatter_tiles = 0;
+    c->tile_ctr[0] = 0;
+    c->tile_ctr[1] = 0;
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+copy_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ copies,
+            const u32 *__restrict__ tile_copy, Counters *__restrict__ ctrs, u32 tile_c, u32 rw)
+{
+    __shared__ u32 s_tile;
+    const u32 n_tiles = ctrs->copy_tiles;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(&ctrs->tile_ctr[2], 1u);
+        __syncthreads();
+        const u32 t = s_tile;
+        __syncthreads();
+        if (t >= n_tiles)
+            break;
+        const WorkItem it = copies[tile_copy[t]];
+        const u64 lo = it.begin + (u64)(t - it.tile_base) * tile_c;
+        const u64 hi = min(it.begin + it.count, lo + tile_c);
+        const u64 w0 = lo * rw, w1 = hi * rw;
+        for (u64 i = w0 + threadIdx.x; i < w1; i += THREADS)
+            in[i] = __ldcs(tmp + i);
+        if (threadIdx.x == 0)
+            atomicAdd(&ctrs->block_bytes, 2ull * (w1 - w0) * 8u);
+    }
+}
+
+cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
+                        u32 cap_b, u32 tile_h, u32 force_grid, cudaStream_t st)
+{
+    init_kernel<<<256, 256, 0, st>>>(ctrs, grid0, blocks, tile_hist, n, top_digit, cap_b, tile_h, force_grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(u64 *hist, u64 *orand, const Counters *ctrs, u32 n_grid_hint, cudaStream_t st)
+{
+    u64 work = (u64)n_grid_hint * RADIX;
+    u64 want = (work + 255) / 256 + 1;
+    u32 blocks = (u32)(want < 4096ull ? want : 4096ull);
+    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, ctrs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st)
+{
+    u32 blocks = n_grid < 65535u ? n_grid : 65535u;
+    if (blocks == 0)
+        blocks = 1;
+    plan_kernel<<<blocks, RADIX, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(Counters *ctrs, cudaStream_t st)
+{
+    advance_kernel<<<1, 1, 0, st>>>(ctrs);
+    return cudaGetLastError();
+}
+
+u32 copy_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (u32)sms * 4u;
+}
+
+cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,
+                        Counters *ctrs, cudaStream_t st)
+{
+    copy_kernel<256><<<copy_grid(), 256, 0, st>>>(in, tmp, copies, tile_copy, ctrs, s.tile_c, s.rw);
+    return cudaGetLastError();
+}
+
+}  // namespace raduls
