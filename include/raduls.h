@@ -96,10 +96,11 @@ typedef struct {
 } raduls_stats;
 
 typedef struct {
-    uint32_t mode;                  /* 0 AUTO, 1 PLAIN, 2 LEARNED */
-    uint32_t learned_log2_buckets;  /* 12..16, 0 = default */
+    uint32_t mode;                  /* 0 AUTO (learned first partition when the top-byte
+                                       histogram is skewed), 1 PLAIN, 2 LEARNED */
+    uint32_t learned_log2_buckets;  /* 12..16, 0 = chosen from n */
     float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio; 0 = 4.0 */
-    uint32_t use_tuned;             /* 1 = use the tuned launch parameters */
+    uint32_t train_steps;           /* Adam steps of the model fit; 0 = 100 */
     raduls_stats *stats;            /* host pointer or NULL */
 } raduls_opts;
 
@@ -122,6 +123,58 @@ int raduls_stream_status(void *stream);
 
 /* Static text for a status code. */
 const char *raduls_status_string(int status);
+
+/* ---- the learned first partition (not in the paper) ----
+ *
+ * A monotone two-level piecewise-linear CDF of key word 0: level 1 is the
+ * exact histogram of the key's top byte over all records (the first MSD
+ * pass's digit histogram, Sec. 1); level 2, per top byte j, maps
+ * t = fp32(key mod 2^56) * 2^-56 through two piecewise-linear stages
+ * u = f2(f1(t)), each with uniformly spaced knots (stage 1 on the range of the
+ * segment's sample, stage 2 on [0, 1]) and learned non-decreasing heights
+ * (cumulative softplus of the parameters, normalised to end at 1).  A key goes
+ * to bucket floor(B * p / n), p = C_j + min(floor(u * R_j), R_j - 1), so
+ * bucket order is key order.  The heights are fitted on the GPU with Adam to
+ * the empirical CDF of a sorted key sample (mean squared error), stage 1
+ * first, then stage 2 on stage 1's output.  raduls_sort_ex(mode = LEARNED, or
+ * AUTO on a skewed top byte) builds one internally; these calls expose the
+ * model for testing and inspection. */
+typedef struct raduls_model raduls_model;
+
+/* Fit a model with 2^log2_buckets buckets (12..16) to the n_recs records at
+ * `in` (device): each stage is warm-started from the sample's CDF at its knots
+ * and refined by train_steps Adam steps.  train_steps = 0 leaves both stages
+ * linear (the untrained model); train_steps = 0x80000000 keeps the warm start
+ * without Adam steps.  *out receives a handle owning its own device buffers. */
+int raduls_model_fit(raduls_model **out, const void *in, uint64_t n_recs, uint32_t rec_bytes,
+                     uint32_t key_bytes, uint32_t log2_buckets, uint32_t train_steps, void *stream);
+
+/* More Adam steps on one stage (0 or 1) with the model's own sample. */
+int raduls_model_train(raduls_model *m, uint32_t stage, uint32_t steps, void *stream);
+
+/* Training loss of one stage (stage 0: f1 alone; stage 1: the whole leaf
+ * f2(f1(t))), as the mean squared CDF error on the sample (host double), and
+ * its gradient w.r.t. that stage's parameters, written into the device float
+ * array d_grad (n_params entries, see raduls_model_sizes; other entries are
+ * left untouched). */
+int raduls_model_loss_grad(raduls_model *m, uint32_t stage, double *h_loss, float *d_grad, void *stream);
+
+/* Bucket of each key word (device u64 in, device u32 out). */
+int raduls_model_buckets(const raduls_model *m, const uint64_t *d_keys, uint64_t n_keys, uint32_t *d_out,
+                         void *stream);
+
+/* Parameter-array length, sample size and log2 of the bucket count. */
+int raduls_model_sizes(const raduls_model *m, uint32_t *n_params, uint32_t *n_sample, uint32_t *log2_buckets);
+
+/* Copy the model to host arrays (any pointer may be NULL): root counts
+ * [256] u64; segment tables [2][256] x {float x0, float inv_w, uint32
+ * first_knot, uint32 knots, uint32 first_param, uint32 pad} (stage 1 then
+ * stage 2); parameters and knot heights [n_params] float; sorted sample
+ * [n_sample] u64. */
+int raduls_model_copy_out(const raduls_model *m, uint64_t *h_root_counts, void *h_segments, float *h_theta,
+                          float *h_heights, uint64_t *h_sample, void *stream);
+
+void raduls_model_free(raduls_model *m);
 
 /* ---- single-step entry points (one kernel each; used to test each step) ---- */
 

@@ -1,0 +1,201 @@
+"""CPU fp64 reference of the learned partitioner -- TEST INFRASTRUCTURE ONLY.
+
+The paper has no learned model; this is the reference for the GPU's
+monotone two-level piecewise-linear CDF model used for the first scatter on
+skewed keys (the GPU kernels share no code with it).  Everything here is
+plain numpy in float64, written from the model's definition:
+
+* Root (level 1): the exact histogram R_j of the top byte j of key word 0
+  over all records (the first MSD pass's digit histogram, Sec. 1 / Fig. 1),
+  with exclusive prefix C_j.
+* Leaf (level 2), one per root segment j: the in-segment coordinate
+  t = fp32(word0 mod 2^56) * 2^-56 in [0, 1) goes through two
+  piecewise-linear stages u = f2(f1(t)); each stage maps its input through
+  knots (x_i, h_i), i = 0..m_j-1.  The knot positions x_i
+  are fixed (the GPU model spaces them uniformly over the range of the
+  segment's sample; knots_from_segments writes them out); the heights are h_0 = 0 and
+  h_i = sum_{l<i} softplus(theta_l) / sum_l softplus(theta_l), so h is
+  non-decreasing and ends at 1 by construction.
+* u(t) = 0 for t < x_0, 1 for t >= x_{m-1}, otherwise with i the last knot
+  index in [0, m-2] with x_i <= t and lam = (t - x_i) / (x_{i+1} - x_i):
+  u = h_i + (h_{i+1} - h_i) * lam.
+* Training loss on a sorted sample of S keys: the mean over samples of
+  (u_s - F_s)^2 with F_s = (r_s + 0.5) / s_j, r_s the sample's rank inside
+  its segment and s_j the segment's sample count; u_s is f1(t_s) when stage 1
+  is trained alone and f2(f1(t_s)) for stage 2.
+* Analytic gradient: with sigma the logistic function and T_j the segment's
+  softplus sum, d u / d theta_l = sigma(theta_l) / T_j * ([l < i] + lam [l == i] - u).
+
+The pins in tests/test_learned_ref.py check this reference against central
+finite differences of its own forward pass, closed-form special cases and a
+planted mistake.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+T_SCALE = 2.0 ** -56
+
+
+def softplus(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x > 30, x, np.log1p(np.exp(np.minimum(x, 30))))
+
+
+def sigmoid(x):
+    x = np.asarray(x, dtype=np.float64)
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def split_keys(keys: np.ndarray):
+    """(segment j, in-segment coordinate t) of u64 key words.
+
+    The model defines t = fp32(key mod 2^56) * 2^-56: the 56-bit remainder is
+    rounded to single precision (round to nearest), then scaled exactly.
+    """
+    keys = np.asarray(keys, dtype=np.uint64)
+    j = (keys >> np.uint64(56)).astype(np.int64)
+    t = (keys & np.uint64((1 << 56) - 1)).astype(np.float32).astype(np.float64) * T_SCALE
+    return j, t
+
+
+def knots_from_segments(seg) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Explicit knot arrays of one stage of uniformly spaced leaves given per
+    segment as (x0, inv_w, first knot, knots, first parameter):
+    returns (knot_off relative to the stage, knot_x with x_i = x0 + i / inv_w,
+    parameter offsets)."""
+    m = np.asarray(seg["m"], dtype=np.int64)
+    off = np.zeros(257, dtype=np.int64)
+    off[1:] = np.cumsum(m)
+    xs = np.zeros(int(off[-1]))
+    for j in range(256):
+        i = np.arange(m[j])
+        xs[off[j]:off[j + 1]] = float(seg["x0"][j]) + i / float(seg["inv_w"][j])
+    return off, xs, np.asarray(seg["poff"], dtype=np.int64)
+
+
+def heights(theta_seg: np.ndarray) -> np.ndarray:
+    """Knot heights of one segment from its m-1 parameters."""
+    sp = softplus(theta_seg)
+    total = sp.sum()
+    h = np.zeros(theta_seg.size + 1)
+    h[1:] = np.cumsum(sp) / total
+    h[-1] = 1.0
+    return h
+
+
+def leaf_u(t: float, x: np.ndarray, h: np.ndarray):
+    """(u, i, lam) of one coordinate; i = -1 outside the knot range."""
+    m = x.size
+    if t < x[0]:
+        return 0.0, -1, 0.0
+    if t >= x[m - 1]:
+        return 1.0, -1, 0.0
+    i = int(np.searchsorted(x[: m - 1], t, side="right") - 1)
+    lam = (t - x[i]) / (x[i + 1] - x[i])
+    return h[i] + (h[i + 1] - h[i]) * lam, i, lam
+
+
+def _seg_layout(sample_sorted, knot_off, poff, coords):
+    j_all, t_all = split_keys(sample_sorted)
+    x_all = t_all if coords is None else np.asarray(coords, dtype=np.float64)
+    if poff is None:
+        poff = np.asarray(knot_off[:256], dtype=np.int64) - np.arange(256)
+    seg_count = np.bincount(j_all, minlength=256)
+    seg_start = np.concatenate([[0], np.cumsum(seg_count)])
+    return x_all, poff, seg_count, seg_start
+
+
+def loss_and_grad(sample_sorted: np.ndarray, knot_off: np.ndarray, knot_x: np.ndarray, theta: np.ndarray,
+                  poff=None, coords=None):
+    """Loss and its analytic gradient w.r.t. theta for one piecewise-linear stage.
+
+    sample_sorted: u64 key words, ascending.  knot_off[j]..knot_off[j+1] are
+    segment j's knots in knot_x; segment j's m_j - 1 parameters start at
+    theta[poff[j]] (default knot_off[j] - j).  coords: the stage's input per
+    sample (default t; the second stage of a leaf takes the first stage's
+    output); inside a segment they must be non-decreasing.
+    """
+    x_all, poff, seg_count, seg_start = _seg_layout(sample_sorted, knot_off, poff, coords)
+    S = sample_sorted.size
+    grad = np.zeros_like(theta, dtype=np.float64)
+    loss = 0.0
+    for j in range(256):
+        a, b = int(knot_off[j]), int(knot_off[j + 1])
+        m = b - a
+        pa = int(poff[j])
+        th = np.asarray(theta[pa: pa + m - 1], dtype=np.float64)
+        x = np.asarray(knot_x[a:b], dtype=np.float64)
+        sj = int(seg_count[j])
+        if sj == 0:
+            continue
+        h = heights(th)
+        sp_total = softplus(th).sum()
+        sg = sigmoid(th)
+        for r in range(sj):
+            s = seg_start[j] + r
+            u, i, lam = leaf_u(x_all[s], x, h)
+            F = (r + 0.5) / sj
+            e = u - F
+            loss += e * e
+            if i < 0:
+                continue
+            ind = (np.arange(m - 1) < i).astype(np.float64)
+            ind[i] += lam
+            grad[pa: pa + m - 1] += 2.0 * e * sg / sp_total * (ind - u)
+    return loss / S, grad / S
+
+
+def loss_only(sample_sorted, knot_off, knot_x, theta, poff=None, coords=None) -> float:
+    x_all, poff, seg_count, seg_start = _seg_layout(sample_sorted, knot_off, poff, coords)
+    S = sample_sorted.size
+    loss = 0.0
+    for j in range(256):
+        a, b = int(knot_off[j]), int(knot_off[j + 1])
+        m = b - a
+        pa = int(poff[j])
+        sj = int(seg_count[j])
+        if sj == 0:
+            continue
+        h = heights(np.asarray(theta[pa: pa + m - 1], dtype=np.float64))
+        x = np.asarray(knot_x[a:b], dtype=np.float64)
+        for r in range(sj):
+            u, _, _ = leaf_u(x_all[seg_start[j] + r], x, h)
+            loss += (u - (r + 0.5) / sj) ** 2
+    return loss / S
+
+
+def stage_output(sample_sorted, knot_off, knot_x, theta, poff=None, coords=None) -> np.ndarray:
+    """Output of one stage for every sample (the next stage's input)."""
+    x_all, poff, seg_count, seg_start = _seg_layout(sample_sorted, knot_off, poff, coords)
+    j_all, _ = split_keys(sample_sorted)
+    out = np.zeros(sample_sorted.size)
+    for j in range(256):
+        if seg_count[j] == 0:
+            continue
+        a, b = int(knot_off[j]), int(knot_off[j + 1])
+        pa = int(poff[j])
+        h = heights(np.asarray(theta[pa: pa + b - a - 1], dtype=np.float64))
+        x = np.asarray(knot_x[a:b], dtype=np.float64)
+        for s in range(int(seg_start[j]), int(seg_start[j + 1])):
+            out[s], _, _ = leaf_u(x_all[s], x, h)
+    return out
+
+
+def bucket_of(keys: np.ndarray, root_counts: np.ndarray, n: int, log2_buckets: int,
+              knot_off: np.ndarray, knot_x: np.ndarray, theta: np.ndarray) -> np.ndarray:
+    """Bucket b = floor(B * p / n), p = C_j + min(floor(u * R_j), R_j - 1) (integer arithmetic)."""
+    j_all, t_all = split_keys(keys)
+    C = np.concatenate([[0], np.cumsum(root_counts.astype(np.int64))])
+    out = np.zeros(keys.size, dtype=np.int64)
+    B = 1 << log2_buckets
+    for idx in range(keys.size):
+        j = int(j_all[idx])
+        a, b = int(knot_off[j]), int(knot_off[j + 1])
+        h = heights(np.asarray(theta[a - j: b - j - 1], dtype=np.float64))
+        u, _, _ = leaf_u(t_all[idx], np.asarray(knot_x[a:b], dtype=np.float64), h)
+        R = int(root_counts[j])
+        q = min(int(np.floor(u * R)), max(R - 1, 0))
+        p = int(C[j]) + q
+        out[idx] = (p * B) // n
+    return out

@@ -8,12 +8,13 @@ built, every call raises.
 """
 from __future__ import annotations
 
-from ._lib import (RaduLSError, STATUS, build_library, library_path, load, raduls_debug_inject,
+from ._lib import (RaduLSError, RaduLSModel, STATUS, build_library, library_path, load, raduls_debug_inject,
                    raduls_distribution_pass, raduls_histogram, raduls_set_wait_limit_ns, raduls_sort,
                    raduls_sort_batched, raduls_sort_ex, raduls_status_string, raduls_stream_status)
 
 __all__ = [
     "RaduLSError",
+    "RaduLSModel",
     "STATUS",
     "build_library",
     "library_path",

@@ -64,7 +64,7 @@ class Opts(ctypes.Structure):
         ("mode", ctypes.c_uint32),
         ("learned_log2_buckets", ctypes.c_uint32),
         ("fallback_ratio", ctypes.c_float),
-        ("use_tuned", ctypes.c_uint32),
+        ("train_steps", ctypes.c_uint32),
         ("stats", ctypes.POINTER(Stats)),
     ]
 
@@ -105,10 +105,20 @@ def load():
             "raduls_debug_inject": [u32, u64],
             "raduls_set_wait_limit_ns": [u64],
         }
+        sigs.update({
+            "raduls_model_fit": [ctypes.POINTER(ctypes.c_void_p), vp, u64, u32, u32, u32, u32, vp],
+            "raduls_model_train": [vp, u32, u32, vp],
+            "raduls_model_loss_grad": [vp, u32, ctypes.POINTER(ctypes.c_double), vp, vp],
+            "raduls_model_buckets": [vp, vp, u64, vp, vp],
+            "raduls_model_sizes": [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)],
+            "raduls_model_copy_out": [vp, vp, vp, vp, vp, vp, vp],
+        })
         for name, args in sigs.items():
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        lib.raduls_model_free.argtypes = [vp]
+        lib.raduls_model_free.restype = None
         lib.raduls_status_string.argtypes = [ctypes.c_int]
         lib.raduls_status_string.restype = ctypes.c_char_p
         _lib = lib
@@ -167,12 +177,12 @@ def raduls_sort(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, stream=No
 
 
 def raduls_sort_ex(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, mode: str = "auto",
-                   learned_log2_buckets: int = 0, fallback_ratio: float = 0.0, use_tuned: bool = True,
+                   learned_log2_buckets: int = 0, fallback_ratio: float = 0.0, train_steps: int = 0,
                    stats: bool = False, stream=None) -> dict | None:
     _check_size(in_, n_recs * rec_bytes, "in")
     _check_size(tmp, n_recs * rec_bytes, "tmp")
     st = Stats()
-    o = Opts(MODES[mode], learned_log2_buckets, fallback_ratio, 1 if use_tuned else 0,
+    o = Opts(MODES[mode], learned_log2_buckets, fallback_ratio, train_steps,
              ctypes.pointer(st) if stats else None)
     rc = load().raduls_sort_ex(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes, ctypes.byref(o),
                                _stream(stream, in_, tmp))
@@ -217,3 +227,59 @@ def raduls_debug_inject(kind: int, tile: int = 0) -> None:
 
 def raduls_set_wait_limit_ns(ns: int) -> None:
     _raise(load().raduls_set_wait_limit_ns(ns), "raduls_set_wait_limit_ns")
+
+
+class RaduLSModel:
+    """Handle of a learned partition model fitted on the GPU (raduls_model_*)."""
+
+    SEG_DTYPE = [("x0", "<f4"), ("inv_w", "<f4"), ("koff", "<u4"), ("m", "<u4"), ("poff", "<u4"),
+                 ("pad", "<u4")]
+
+    def __init__(self, in_, n_recs: int, rec_bytes: int, key_bytes: int, log2_buckets: int = 16,
+                 train_steps: int = 100, stream=None):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        rc = self._lib.raduls_model_fit(ctypes.byref(self._h), _addr(in_), n_recs, rec_bytes, key_bytes,
+                                        log2_buckets, train_steps, _stream(stream, in_))
+        _raise(rc, "raduls_model_fit")
+        np_, ns, lb = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _raise(self._lib.raduls_model_sizes(self._h, ctypes.byref(np_), ctypes.byref(ns), ctypes.byref(lb)),
+               "raduls_model_sizes")
+        self.n_params, self.n_sample, self.log2_buckets = np_.value, ns.value, lb.value
+
+    def train(self, stage: int, steps: int, stream=None) -> None:
+        _raise(self._lib.raduls_model_train(self._h, stage, steps, _stream(stream)), "raduls_model_train")
+
+    def loss_grad(self, stage: int, grad_out, stream=None) -> float:
+        loss = ctypes.c_double()
+        _raise(self._lib.raduls_model_loss_grad(self._h, stage, ctypes.byref(loss), _addr(grad_out),
+                                                _stream(stream, grad_out)), "raduls_model_loss_grad")
+        return loss.value
+
+    def buckets(self, keys, out, stream=None) -> None:
+        n = keys.numel() if hasattr(keys, "numel") else 0
+        _raise(self._lib.raduls_model_buckets(self._h, _addr(keys), n, _addr(out), _stream(stream, keys)),
+               "raduls_model_buckets")
+
+    def copy_out(self) -> dict:
+        import numpy as np
+        root = np.zeros(256, dtype=np.uint64)
+        seg = np.zeros((2, 256), dtype=self.SEG_DTYPE)
+        theta = np.zeros(self.n_params, dtype=np.float32)
+        heights = np.zeros(self.n_params, dtype=np.float32)
+        sample = np.zeros(self.n_sample, dtype=np.uint64)
+        _raise(self._lib.raduls_model_copy_out(self._h, root.ctypes.data, seg.ctypes.data, theta.ctypes.data,
+                                               heights.ctypes.data, sample.ctypes.data, None),
+               "raduls_model_copy_out")
+        return {"root": root, "seg": seg, "theta": theta, "heights": heights, "sample": sample}
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.raduls_model_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

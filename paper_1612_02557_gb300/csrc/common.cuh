@@ -15,6 +15,9 @@ typedef unsigned long long u64;
 typedef unsigned int u32;
 
 constexpr int RADIX = 256;
+// Sub-bins of at most WARP_BIN records are packed into runs and sorted by one
+// warp each on chip; the planner and the on-chip sort share this bound.
+constexpr unsigned WARP_BIN = 256;
 constexpr u32 FULL_MASK = 0xffffffffu;
 
 // Status codes shared with the C ABI (raduls.h).
@@ -38,7 +41,11 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
 
-enum : u32 { ITEM_IN_TMP = 1u };
+// ITEM_IN_TMP: the records currently sit in tmp.  ITEM_RUN (block items): the
+// item is a run of sub-bins of one parent, grouped by the parent's digit.
+// ITEM_SEG (with ITEM_RUN): a run of consecutive independent arrays of a
+// batched sort, arrays [tile_base, tile_base + row) of the offset table.
+enum : u32 { ITEM_IN_TMP = 1u, ITEM_RUN = 2u, ITEM_SEG = 4u };
 
 // Device-side counters of one sort.  All list lengths live here so that the
 // pass kernels never need the host to know them.
@@ -60,7 +67,9 @@ struct Counters {
     u64 scatter_bytes;    // algorithmic bytes read+written by distribution tiles
     u64 block_bytes;      // bytes read+written by on-chip sorts and copies
     u32 levels;
-    u32 pad;
+    u32 learned_ok;       // 1 while the learned partition passes its balance check
+    float learned_ratio;  // max bucket / ideal bucket of the learned partition (0 = not measured)
+    u32 learned_fell_back;
 };
 
 // Capacities of the device lists (set by the host from n and the tile sizes).
@@ -73,6 +82,126 @@ struct Caps {
     u32 pad;
     u64 block;      // block items
 };
+
+// ---------------------------------------------------------------- learned model
+//
+// Monotone two-level piecewise-linear CDF of key word 0 (the learned first
+// partition).  Level 1 (root): segment j = top byte of the key, with the exact
+// record count R_j of the segment (the first MSD pass's digit histogram) and
+// its exclusive prefix C_j.  Level 2 (leaf, one per segment): the in-segment
+// coordinate t = fp32(key mod 2^56) * 2^-56 goes through two piecewise-linear
+// stages, u = f2(f1(t)).  Each stage has m uniformly spaced knots (stage 1 on
+// the range of the segment's sample, stage 2 on [0, 1]) with learned
+// non-decreasing heights (h_0 = 0, h_{m-1} = 1); a trained stage 1 stretches
+// dense regions of t over their share of [0, 1], so stage 2's uniform knots
+// resolve them.  A key's rank estimate is p = C_j + min(floor(u * R_j), R_j - 1)
+// and its bucket b = floor(p * B / n), B = 2^log2B; every step is monotone in
+// the key, so bucket order is key order.  The bucket id is used as two MSD
+// "digits": its top 8 bits and its low (log2B - 8) bits.
+
+constexpr u32 DIGIT_LEARNED_HI = 0x10000u;  // digit code: top 8 bits of the model bucket
+constexpr u32 DIGIT_LEARNED_LO = 0x10001u;  // digit code: low bits of the model bucket
+
+struct ModelSeg {
+    float x0;     // first knot
+    float inv_w;  // 1 / knot spacing
+    u32 koff;     // first knot (height) index
+    u32 m;        // knots (>= 2)
+    u32 poff;     // first parameter index (m - 1 parameters)
+    u32 pad;
+};
+
+struct Model {
+    ModelSeg seg[2][RADIX];  // stage 1 and stage 2 of every segment's leaf
+    u64 root_cnt[RADIX];
+    u64 root_c[RADIX];
+    const float *h;          // knot heights of both stages (device)
+    const u64 *heavy;        // sorted keys that alone fill >= 4 ideal buckets in the sample
+    u64 n;                   // records the model partitions
+    u32 log2b;               // log2 of the bucket count (12..16)
+    u32 lo_bits;             // log2b - 8
+    u32 n_heavy;
+    u32 pad;
+};
+
+constexpr u32 HEAVY_MAX = 2048;  // heavy keys tracked for the balance check
+
+// Is `key` one of the model's heavy keys (binary search of a sorted list)?
+__device__ __forceinline__ bool is_heavy(const u64 *list, u32 n, u64 key)
+{
+    u32 a = 0, b = n;
+    while (a < b) {
+        const u32 mid = (a + b) >> 1;
+        if (list[mid] < key)
+            a = mid + 1;
+        else
+            b = mid;
+    }
+    return a < n && list[a] == key;
+}
+
+// One piecewise-linear stage at coordinate x.
+__device__ __forceinline__ float pl_stage(const ModelSeg &sg, const float *__restrict__ h, float x)
+{
+    const float g = (x - sg.x0) * sg.inv_w;
+    if (!(g > 0.f))
+        return 0.f;
+    if (g >= (float)(sg.m - 1u))
+        return 1.f;
+    u32 i = (u32)g;
+    if (i > sg.m - 2u)
+        i = sg.m - 2u;
+    const float lam = g - (float)i;
+    const float h0 = h[sg.koff + i], h1 = h[sg.koff + i + 1];
+    return fminf(fmaxf(fmaf(h1 - h0, lam, h0), h0), h1);
+}
+
+__device__ __forceinline__ u32 model_bucket(const Model *__restrict__ M, u64 key)
+{
+    const u32 j = (u32)(key >> 56);
+    const float t = (float)(key & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
+    const float u = pl_stage(M->seg[1][j], M->h, pl_stage(M->seg[0][j], M->h, t));
+    const u64 r = M->root_cnt[j];
+    u64 q = (u64)((double)u * (double)r);
+    if (q >= r)
+        q = r ? r - 1 : 0;
+    return (u32)(((M->root_c[j] + q) << M->log2b) / M->n);
+}
+
+// Which digit a pass splits on: a key byte (word, shift) or a model digit.
+struct DigitSel {
+    u32 word;
+    u32 shift;
+    u32 learned;  // 0 key byte, 1 model bucket top bits, 2 model bucket low bits
+};
+
+__device__ __forceinline__ DigitSel digit_sel(u32 digit, u32 key_words)
+{
+    DigitSel s;
+    if (digit >= DIGIT_LEARNED_HI) {
+        s.word = 0;
+        s.shift = 0;
+        s.learned = digit - DIGIT_LEARNED_HI + 1u;
+    } else {
+        s.word = key_words - 1u - digit / 8u;
+        s.shift = 8u * (digit % 8u);
+        s.learned = 0;
+    }
+    return s;
+}
+
+__device__ __forceinline__ u32 digit_of_key(const DigitSel &s, u64 key_word, const Model *M)
+{
+    if (s.learned == 0)
+        return (u32)(key_word >> s.shift) & 0xffu;
+    const u32 b = model_bucket(M, key_word);
+    return s.learned == 1 ? (b >> M->lo_bits) : (b & ((1u << M->lo_bits) - 1u));
+}
+
+__device__ __forceinline__ u32 digit_of(const DigitSel &s, const u64 *rec, const Model *M)
+{
+    return digit_of_key(s, rec[s.word], M);
+}
 
 // Look-back status word: flag (2 bits) | epoch (22 bits) | value (40 bits).
 // The epoch changes for every distribution launch, so stale words from an
@@ -117,6 +246,60 @@ __device__ __forceinline__ u32 lanemask_lt()
     u32 m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// ---- mbarrier + bulk asynchronous copy (TMA engine), inline PTX -----------
+
+__device__ __forceinline__ u32 smem_u32(const void *p)
+{
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64 *bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later asynchronous-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0), completing
+// on mbarrier `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, u32 bytes, u64 *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void set_error(Counters *c, u32 code)
@@ -193,14 +376,36 @@ struct RankSmem {
     u32 wsum[RADIX / 32];
 };
 
+// Lanes of the warp holding the same digit as this lane (warp multi-split,
+// Ashkiani et al., "GPU Multisplit", 2016): one ballot per digit bit, each
+// lane keeps the lanes that agree with it on that bit (NB = 8 bits).
+template <int NB>
+__device__ __forceinline__ u32 peers_of(u32 d)
+{
+    u32 peers = FULL_MASK;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const u32 bal = __ballot_sync(FULL_MASK, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // Phase 1 of a stable block ranking (used by the distribution pass and the
 // on-chip sort).  Elements are laid out warp-contiguously: warp w owns
 // elements [w*32*K, (w+1)*32*K), lane l holds element w*32*K + k*32 + l in slot
-// k.  dig[k] is the element's digit, or RADIX for padding.  Each warp ranks its
-// elements in order with __match_any_sync, so equal digits keep element order;
-// rk[k] is the rank among the warp's earlier elements with the same digit.
+// k.  On entry dr[k] is the element's digit.  Padding elements (the tail of a
+// partial tile) carry digit RADIX-1: they come after every real element in
+// element order, so they rank behind all real elements of the last digit and
+// leave every real element's rank unchanged; callers drop them and subtract
+// them from the last digit's total.  Each warp ranks its elements in order, so
+// equal digits keep element order.  On exit dr[k] = digit | rank << 8, where
+// rank counts the warp's earlier elements with the same digit.
+// Only slots k < kv are used (kv = K for full tiles); a slot whose first
+// element is past the valid count m is all padding and is skipped.
 template <int THREADS, int K>
-__device__ __forceinline__ void warp_rank(RankSmem<THREADS> &sm, const u32 (&dig)[K], u32 (&rk)[K])
+__device__ __forceinline__ void warp_rank(RankSmem<THREADS> &sm, u32 (&dr)[K], u32 kv = K, u32 m = ~0u)
 {
     const u32 lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
     u32 *cnt = sm.cnt[w];
@@ -210,14 +415,16 @@ __device__ __forceinline__ void warp_rank(RankSmem<THREADS> &sm, const u32 (&dig
     const u32 lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const u32 d = dig[k];
-        const u32 peers = __match_any_sync(FULL_MASK, d);
+        if ((u32)k >= kv || w * 32u * kv + (u32)k * 32u >= m)
+            break;
+        const u32 d = dr[k];
+        const u32 peers = peers_of<8>(d);
         const u32 prev = cnt[d];
         __syncwarp();
         if ((peers & lt) == 0)  // lowest lane of the peer group updates the counter
             cnt[d] = prev + __popc(peers);
         __syncwarp();
-        rk[k] = prev + __popc(peers & lt);
+        dr[k] = d | ((prev + __popc(peers & lt)) << 8);
     }
 }
 
@@ -234,6 +441,36 @@ __device__ __forceinline__ u32 warp_offsets(RankSmem<THREADS> &sm, u32 d)
         s += c;
     }
     return s;
+}
+
+// Named barrier among the first `count` threads (a multiple of 32).
+__device__ __forceinline__ void bar_sync_named(u32 id, u32 count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Exclusive scan of the 256 digit totals held by threads 0..255 into
+// sm.tstart, synchronising only those 256 threads (named barrier 1), so the
+// other warps of the block can do independent work meanwhile.
+template <int THREADS>
+__device__ __forceinline__ void scan_totals_256(RankSmem<THREADS> &sm, u32 total)
+{
+    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    u32 incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 v = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= (u32)o)
+            incl += v;
+    }
+    if (lane == 31)
+        sm.wsum[w] = incl;
+    bar_sync_named(1, RADIX);
+    u32 add = 0;
+#pragma unroll
+    for (int i = 0; i < RADIX / 32; ++i)
+        add += (i < (int)w) ? sm.wsum[i] : 0u;
+    sm.tstart[tid] = add + incl - total;
 }
 
 // Phase 3: exclusive scan of the 256 digit totals held by threads 0..255

@@ -43,6 +43,14 @@ Shape choose_shape(u32 rw, u32 key_words)
         s.scat_var = 4;
         s.block_var = 4;
     }
+    if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
+        const int want = atoi(v);
+        const bool fits = (want == 10 && rw == 1) || ((want == 11 || want == 13 || want == 14) && rw == 2) ||
+                          ((want == 12 || want == 15) && rw == 4) || (want == 0 && rw == 1) ||
+                          ((want == 1 || want == 5 || want == 6 || want == 7) && rw == 2) || (want == 2 && rw == 4);
+        if (fits)
+            s.scat_var = want;
+    }
     s.tile_s = scatter_tile_of(s.scat_var);
     s.cap_b = block_cap_of(s.block_var);
     return s;
@@ -57,14 +65,33 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// One set of pass buffers with its own device counters: the main sort uses
+// one, the nested sort of the learned model's key sample the other.
+struct Work {
+    Counters *ctrs = nullptr;    // device
+    Counters *h_ctrs = nullptr;  // pinned host mirror
+    DevBuf lists, hist, status, tiles;
+    u32 epoch = 0;
+};
+
+// Device buffers of one learned model (see the Model struct in common.cuh).
+struct ModelBufs {
+    DevBuf buf;
+    Model *model = nullptr;
+    float *h = nullptr, *theta = nullptr, *am = nullptr, *av = nullptr, *tot = nullptr;
+    double *E = nullptr, *G = nullptr, *Z = nullptr, *loss = nullptr;
+    u64 *sample = nullptr, *sample_tmp = nullptr, *root = nullptr, *heavy = nullptr;
+    u32 *seg_start = nullptr;
+    u32 S = 0, k_extra = 0, max_knots = 0, n_params_cap = 0, steps_done = 0;
+    u32 log2b = 0;
+};
+
 struct Ctx {
     std::mutex mu;
     bool inited = false;
-    Counters *ctrs = nullptr;      // device
-    Counters *h_ctrs = nullptr;    // pinned host mirror
-    u32 *dev_status = nullptr;     // device: sticky status word of this device
-    DevBuf lists, hist, status, tiles;
-    u32 epoch = 0;
+    u32 *dev_status = nullptr;   // device: sticky status word of this device
+    Work main, aux;
+    ModelBufs mdl;
     u64 wait_ns = 2000000000ull;
     u32 inject_tile = ~0u;
     cudaEvent_t ev[1024] = {};
@@ -155,11 +182,25 @@ int check_args(const void *in, const void *tmp, u64 n, u32 rec_bytes, u32 key_by
     return RADULS_OK;
 }
 
+cudaError_t work_init(Work &w)
+{
+    cudaError_t e = cudaMalloc(&w.ctrs, sizeof(Counters));
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemset(w.ctrs, 0, sizeof(Counters));
+    if (e != cudaSuccess)
+        return e;
+    return cudaMallocHost(&w.h_ctrs, sizeof(Counters));
+}
+
 cudaError_t ctx_init(Ctx &c)
 {
     if (c.inited)
         return cudaSuccess;
-    cudaError_t e = cudaMalloc(&c.ctrs, sizeof(Counters));
+    cudaError_t e = work_init(c.main);
+    if (e != cudaSuccess)
+        return e;
+    e = work_init(c.aux);
     if (e != cudaSuccess)
         return e;
     e = cudaMalloc(&c.dev_status, 256);
@@ -168,22 +209,20 @@ cudaError_t ctx_init(Ctx &c)
     e = cudaMemset(c.dev_status, 0, 256);
     if (e != cudaSuccess)
         return e;
-    e = cudaMallocHost(&c.h_ctrs, sizeof(Counters));
-    if (e != cudaSuccess)
-        return e;
     c.inited = true;
     return cudaSuccess;
 }
 
-// Sizes every list for a problem of n records (upper bounds, see below).
-cudaError_t ctx_lists(Ctx &c, const Shape &s, u64 n, Lists &L)
+// Sizes every list for a problem of n records (upper bounds).
+cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
 {
     const u64 W = s.key_words;
     const u64 grid_cap = n / ((u64)s.cap_b + 1) + 2;                 // grid bins hold > cap_b records each
     const u64 hist_tiles = n / s.tile_h + grid_cap + 2;
     const u64 copy_cap = 8 * W * grid_cap + 2;                        // one per finished big bin
     const u64 copy_tiles = n / s.tile_c + copy_cap + 2;
-    u64 block_cap = 2 * n / s.cap_b + 2 * 8 * W * grid_cap + 4;       // full runs + runs cut by big bins/parents
+    // full runs + runs cut by big bins / parents + the model's sub-bins (<= 2^16)
+    u64 block_cap = 2 * n / s.cap_b + 2 * 8 * W * grid_cap + 4 + 65536 + 256;
     if (block_cap > n + 4)
         block_cap = n + 4;
     if (grid_cap > 0xffffffffull || hist_tiles > 0xffffffffull || copy_tiles > 0xffffffffull)
@@ -196,10 +235,10 @@ cudaError_t ctx_lists(Ctx &c, const Shape &s, u64 n, Lists &L)
     o_copies = off; off = align256(off + copy_cap * sizeof(WorkItem));
     o_th = off; off = align256(off + hist_tiles * 4);
     o_tc = off; off = align256(off + copy_tiles * 4);
-    cudaError_t e = ensure(c.lists, off, false);
+    cudaError_t e = ensure(wk.lists, off, false);
     if (e != cudaSuccess)
         return e;
-    char *b = (char *)c.lists.p;
+    char *b = (char *)wk.lists.p;
     L.grid[0] = (WorkItem *)(b + o_grid0);
     L.grid[1] = (WorkItem *)(b + o_grid1);
     L.scat = (WorkItem *)(b + o_scat);
@@ -216,45 +255,51 @@ cudaError_t ctx_lists(Ctx &c, const Shape &s, u64 n, Lists &L)
     return cudaSuccess;
 }
 
-// Per-level buffers: histogram rows of the current big bins and the look-back
-// status words of this level's distribution tiles.
-cudaError_t ctx_level(Ctx &c, const Shape &s, u64 n, u32 n_grid, u64 **hist, u64 **orand, u64 **status,
-                      u32 **tile_scat, Caps &caps, cudaStream_t st)
+struct LevelBufs {
+    u64 *hist, *orand, *dlight, *status;
+    u32 *tile_scat;
+};
+
+// Per-level buffers: histogram rows (and OR/AND words) of the current big bins
+// and the look-back status words of this level's distribution tiles.
+cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B, Caps &caps, cudaStream_t st)
 {
     const u64 rows = (u64)n_grid + 1;
-    cudaError_t e = ensure(c.hist, align256(rows * RADIX * 8) + rows * 16, false);
+    const size_t hb = align256(rows * RADIX * 8), ob = align256(rows * 16), db = rows * RADIX * 8;
+    cudaError_t e = ensure(wk.hist, hb + ob + db, false);
     if (e != cudaSuccess)
         return e;
-    *hist = (u64 *)c.hist.p;
-    *orand = (u64 *)((char *)c.hist.p + align256(rows * RADIX * 8));
+    B.hist = (u64 *)wk.hist.p;
+    B.orand = (u64 *)((char *)wk.hist.p + hb);
+    B.dlight = (u64 *)((char *)wk.hist.p + hb + ob);
     const u64 st_tiles = n / s.tile_s + n_grid + 2;
     if (st_tiles > 0xffffffffull)
         return cudaErrorInvalidValue;
     bool grew = false;
-    e = ensure(c.status, st_tiles * RADIX * 8, true, &grew, st);
+    e = ensure(wk.status, st_tiles * RADIX * 8, true, &grew, st);
     if (e != cudaSuccess)
         return e;
     if (grew)
-        c.epoch = 0;
-    e = ensure(c.tiles, st_tiles * 4, false);
+        wk.epoch = 0;
+    e = ensure(wk.tiles, st_tiles * 4, false);
     if (e != cudaSuccess)
         return e;
-    *status = (u64 *)c.status.p;
-    *tile_scat = (u32 *)c.tiles.p;
-    caps.scat_tiles = (u32)(c.status.bytes / (RADIX * 8));
-    if ((u64)caps.scat_tiles * 4 > c.tiles.bytes)
-        caps.scat_tiles = (u32)(c.tiles.bytes / 4);
+    B.status = (u64 *)wk.status.p;
+    B.tile_scat = (u32 *)wk.tiles.p;
+    caps.scat_tiles = (u32)(wk.status.bytes / (RADIX * 8));
+    if ((u64)caps.scat_tiles * 4 > wk.tiles.bytes)
+        caps.scat_tiles = (u32)(wk.tiles.bytes / 4);
     return cudaSuccess;
 }
 
-u32 next_epoch(Ctx &c, cudaStream_t st)
+u32 next_epoch(Work &wk, cudaStream_t st)
 {
-    c.epoch += 1;
-    if (c.epoch >= LB_EPOCH_MASK) {
-        cudaMemsetAsync(c.status.p, 0, c.status.bytes, st);
-        c.epoch = 1;
+    wk.epoch += 1;
+    if (wk.epoch >= LB_EPOCH_MASK) {
+        cudaMemsetAsync(wk.status.p, 0, wk.status.bytes, st);
+        wk.epoch = 1;
     }
-    return c.epoch;
+    return wk.epoch;
 }
 
 // Times each launch with a pair of CUDA events on the launching stream when
@@ -296,6 +341,10 @@ struct SortJob {
     u32 digit;
     u64 *hist_out;         // histogram-only mode when non-null
     raduls_stats *stats;
+    u32 mode;              // 0 auto, 1 plain, 2 learned
+    u32 log2b;             // learned buckets (0 = chosen from n)
+    float fallback_ratio;  // learned partition rejected above this
+    u32 train_steps;
 };
 
 #define CK(x)                               \
@@ -325,21 +374,140 @@ cudaError_t ctx_events(Ctx &c)
     return cudaSuccess;
 }
 
-int run_sort(Ctx &c, const SortJob &j, cudaStream_t st)
+int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *outer = nullptr);
+
+// ------------------------------------------------------------ learned model
+
+constexpr u32 SAMPLE_MAX = 1u << 20;
+constexpr u32 K_EXTRA_MAX = 1u << 14;
+
+// Device buffers of a model for sample size S and knot budget k_extra.
+cudaError_t model_bufs(ModelBufs &M, u32 S, u32 k_extra)
+{
+    const u32 knots = 2u * (2u * RADIX + k_extra) + 8u;  // both stages
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_model = take(sizeof(Model)), o_h = take(knots * 4), o_th = take(knots * 4),
+                 o_am = take(knots * 4), o_av = take(knots * 4), o_tot = take(2 * RADIX * 4), o_E = take(knots * 8),
+                 o_G = take(knots * 8), o_Z = take(RADIX * 8), o_loss = take(8), o_s = take((size_t)S * 8),
+                 o_st = take((size_t)S * 8), o_root = take(RADIX * 8), o_seg = take((RADIX + 1) * 4),
+                 o_heavy = take(HEAVY_MAX * 8);
+    cudaError_t e = ensure(M.buf, off, true);
+    if (e != cudaSuccess)
+        return e;
+    char *b = (char *)M.buf.p;
+    M.model = (Model *)(b + o_model);
+    M.h = (float *)(b + o_h);
+    M.theta = (float *)(b + o_th);
+    M.am = (float *)(b + o_am);
+    M.av = (float *)(b + o_av);
+    M.tot = (float *)(b + o_tot);
+    M.E = (double *)(b + o_E);
+    M.G = (double *)(b + o_G);
+    M.Z = (double *)(b + o_Z);
+    M.loss = (double *)(b + o_loss);
+    M.sample = (u64 *)(b + o_s);
+    M.sample_tmp = (u64 *)(b + o_st);
+    M.root = (u64 *)(b + o_root);
+    M.seg_start = (u32 *)(b + o_seg);
+    M.heavy = (u64 *)(b + o_heavy);
+    M.S = S;
+    M.k_extra = k_extra;
+    M.max_knots = 2u + k_extra;
+    M.n_params_cap = knots;
+    return cudaSuccess;
+}
+
+
+
+constexpr float LEARN_RATE = 0.05f;
+
+// Fit a model of the key words 0 of `in` (n records of rw words) whose exact
+// top-byte histogram is root_hist (device, 256 u64): sample, sort the sample
+// with the aux work set, build the leaves, run `steps` Adam steps.
+int model_fit(Ctx &c, ModelBufs &M, const u64 *in, u64 n, u32 rw, const u64 *root_hist, u32 log2b, u32 steps,
+              cudaStream_t st, Recorder &rec, bool warm_only = false)
+{
+    u32 S = n < (u64)SAMPLE_MAX ? (u32)n : SAMPLE_MAX;
+    if (S < 2)
+        S = 2;
+    u32 k_extra = S / 8u;
+    if (k_extra > K_EXTRA_MAX)
+        k_extra = K_EXTRA_MAX;
+    CK(model_bufs(M, S, k_extra));
+    M.log2b = log2b;
+    CK(cudaMemcpyAsync(M.root, root_hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
+    TIMED(RADULS_K_LEARNED, lm_launch_sample(in, n, rw, S, M.sample, st));
+    SortJob sj{};
+    sj.in = M.sample;
+    sj.tmp = M.sample_tmp;
+    sj.n = S;
+    sj.rw = 1;
+    sj.kw = 1;
+    sj.mode = 1;
+    int rc = run_sort(c, c.aux, sj, st, &rec);
+    if (rc)
+        return rc;
+    TIMED(RADULS_K_LEARNED, lm_launch_build(M.sample, S, k_extra, M.root, n, log2b, M.h, M.model, M.seg_start,
+                                            M.max_knots, st));
+    TIMED(RADULS_K_LEARNED, lm_launch_init(M.theta, M.am, M.av, M.n_params_cap, st));
+    {
+        // a key filling >= 4 ideal buckets' worth of the sample is unsplittable
+        const u64 thr = (4ull * S) >> log2b;
+        TIMED(RADULS_K_LEARNED, lm_launch_heavy(M.sample, S, (u32)(thr > 1 ? thr : 2), M.heavy, M.model, st));
+    }
+    // stage 1 on its own, then stage 2 on stage 1's output: each warm-started
+    // from the sample's CDF at its knots, then `steps` Adam steps (steps = 0
+    // keeps both stages linear: the untrained model)
+    for (u32 stage = 0; stage < 2 && steps > 0; ++stage) {
+        if (stage == 1)
+            TIMED(RADULS_K_LEARNED, lm_launch_heights(M.model, M.theta, M.h, M.tot, M.E, M.G, M.Z, M.loss, st));
+        TIMED(RADULS_K_LEARNED, lm_launch_warm(M.model, stage, M.sample, M.seg_start, M.theta, st));
+        if (warm_only)
+            continue;
+        for (u32 k = 1; k <= steps; ++k)
+            TIMED(RADULS_K_LEARNED, lm_launch_step(M.model, stage, M.theta, M.am, M.av, M.h, M.tot, M.E, M.G, M.Z,
+                                                   M.loss, M.sample, M.seg_start, S, LEARN_RATE, (int)k, nullptr,
+                                                   st));
+    }
+    M.steps_done = steps;
+    TIMED(RADULS_K_LEARNED, lm_launch_heights(M.model, M.theta, M.h, M.tot, M.E, M.G, M.Z, M.loss, st));
+    return RADULS_OK;
+}
+
+u32 default_log2b(u64 n, u32 cap_b)
+{
+    u32 l = 12;
+    while (l < 16 && (n >> l) > cap_b)
+        ++l;
+    return l;
+}
+
+// ---------------------------------------------------------------- the sort
+
+int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *outer)
 {
     const Shape s = choose_shape(j.rw, j.kw);
     Lists L{};
-    CK(ctx_lists(c, s, j.n, L));
-    Recorder rec;
-    rec.c = &c;
-    rec.st = st;
-    if (j.stats) {
-        CK(ctx_events(c));
-        rec.timing = true;
+    CK(work_lists(wk, s, j.n, L));
+    Recorder own;
+    Recorder &rec = outer ? *outer : own;
+    if (!outer) {
+        rec.c = &c;
+        rec.st = st;
+        if (j.stats) {
+            CK(ctx_events(c));
+            rec.timing = true;
+        }
     }
     const u32 top = 8u * j.kw - 1u;
     const bool step_api = j.single_pass || j.hist_out;
-    TIMED(RADULS_K_SETUP, launch_init(c.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, step_api ? j.digit : top,
+    const bool may_learn = !step_api && j.mode != 1 && j.n > s.cap_b;
+    TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, step_api ? j.digit : top,
                                       s.cap_b, s.tile_h, step_api ? 1u : 0u, st));
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
@@ -347,65 +515,99 @@ int run_sort(Ctx &c, const SortJob &j, cudaStream_t st)
         c.inject_tile = g_inject_tile;
         g_inject_tile = ~0u;
     }
+    bool learned = false;
+    float ratio_limit = j.fallback_ratio > 0.f ? j.fallback_ratio : 4.f;
     int cur = 0;
     u32 n_grid = (step_api || j.n > s.cap_b) ? 1u : 0u;
     for (u32 level = 0; n_grid > 0; ++level) {
-        u64 *hist, *orand, *status;
-        u32 *tile_scat;
-        CK(ctx_level(c, s, j.n, n_grid, &hist, &orand, &status, &tile_scat, L.caps, st));
-        TIMED(RADULS_K_SETUP, launch_prep(hist, orand, c.ctrs, n_grid, st));
-        TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, hist, orand, c.ctrs, st));
+        LevelBufs B{};
+        CK(work_level(wk, s, j.n, n_grid, B, L.caps, st));
+        const Model *model = learned ? c.mdl.model : nullptr;
+        TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
+        TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
+                                         wk.ctrs, model, st));
         if (j.hist_out) {
-            CK(cudaMemcpyAsync(j.hist_out, hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(j.hist_out, B.hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
             break;
         }
+        if (level == 0 && may_learn) {
+            // the first pass's digit histogram decides (auto) and is the model's root
+            bool use = (j.mode == 2);
+            if (!use) {
+                u64 h[RADIX];
+                CK(cudaMemcpyAsync(h, B.hist, sizeof h, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                u64 mx = 0;
+                for (int d = 0; d < RADIX; ++d)
+                    mx = h[d] > mx ? h[d] : mx;
+                use = mx > 4ull * (j.n / RADIX) && j.kw >= 1;
+            }
+            if (use) {
+                const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
+                int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);
+                if (rc)
+                    return rc;
+                learned = true;
+                // restart the level on the model's top digit
+                TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, DIGIT_LEARNED_HI,
+                                                  s.cap_b, s.tile_h, 1u, st));
+                TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
+                TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand,
+                                                 B.dlight, wk.ctrs, c.mdl.model, st));
+                model = c.mdl.model;
+            }
+        }
+        if (learned && level == 1)
+            TIMED(RADULS_K_LEARNED, lm_launch_ratio(B.dlight, wk.ctrs, c.mdl.model, ratio_limit, st));
         PlanArgs a{};
         a.grid_cur = L.grid[cur];
         a.grid_next = L.grid[cur ^ 1];
         a.scat = L.scat;
         a.blocks = L.blocks;
         a.copies = L.copies;
-        a.hist = hist;
-        a.orand = orand;
+        a.hist = B.hist;
+        a.orand = B.orand;
         a.tile_hist = L.tile_hist;
-        a.tile_scat = tile_scat;
+        a.tile_scat = B.tile_scat;
         a.tile_copy = L.tile_copy;
-        a.ctrs = c.ctrs;
+        a.ctrs = wk.ctrs;
         a.caps = L.caps;
         a.key_words = j.kw;
         a.rw = j.rw;
         a.cap_b = s.cap_b;
+        a.warp_bin = WARP_BIN;
         a.tile_h = s.tile_h;
         a.tile_s = s.tile_s;
         a.tile_c = s.tile_c;
         a.single_pass = j.single_pass ? 1u : 0u;
+        a.top_digit = top;
         TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-        const u32 epoch = next_epoch(c, st);
-        TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, tile_scat, hist, status, c.ctrs, epoch,
-                                               c.wait_ns, c.inject_tile, st));
+        const u32 epoch = next_epoch(wk, st);
+        TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs,
+                                               epoch, c.wait_ns, c.inject_tile, model, st));
         c.inject_tile = ~0u;
-        TIMED(RADULS_K_SETUP, launch_advance(c.ctrs, st));
+        TIMED(RADULS_K_SETUP, launch_advance(wk.ctrs, st));
         if (j.single_pass)
             break;
-        CK(cudaMemcpyAsync(c.h_ctrs, c.ctrs, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(wk.h_ctrs, wk.ctrs, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (c.h_ctrs->err)
+        if (wk.h_ctrs->err)
             break;
-        n_grid = c.h_ctrs->grid_cur;
+        n_grid = wk.h_ctrs->grid_cur;
         cur ^= 1;
     }
     if (!step_api) {
-        TIMED(RADULS_K_COPY, launch_copy(s, j.in, j.tmp, L.copies, L.tile_copy, c.ctrs, st));
-        TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks, c.ctrs, st));
+        TIMED(RADULS_K_COPY, launch_copy(s, j.in, j.tmp, L.copies, L.tile_copy, wk.ctrs, st));
+        TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks, wk.ctrs, nullptr, st));
     }
     CK(rec.begin(RADULS_K_SETUP));
-    fold_status_kernel<<<1, 1, 0, st>>>(c.ctrs, c.dev_status);
+    fold_status_kernel<<<1, 1, 0, st>>>(wk.ctrs, c.dev_status);
     CK(cudaGetLastError());
     CK(rec.end());
-    if (j.stats) {
-        CK(cudaMemcpyAsync(c.h_ctrs, c.ctrs, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    if (j.stats && !outer) {
+        CK(cudaMemcpyAsync(wk.h_ctrs, wk.ctrs, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const Counters &h = *c.h_ctrs;
+        const Counters &h = *wk.h_ctrs;
         raduls_stats &o = *j.stats;
         o.grid_passes = h.grid_passes;
         o.levels = h.levels;
@@ -414,6 +616,9 @@ int run_sort(Ctx &c, const SortJob &j, cudaStream_t st)
         o.block_bytes = h.block_bytes;
         o.block_items = h.block;
         o.skipped_digits = h.skipped;
+        o.learned_used = learned ? 1u : 0u;
+        o.learned_fell_back = learned ? h.learned_fell_back : 0u;
+        o.learned_ratio = learned ? h.learned_ratio : 0.f;
         o.gpu_launches = rec.total;
         for (int k = 0; k < RADULS_K_COUNT; ++k) {
             o.kernel_launches[k] = rec.launches[k];
@@ -445,6 +650,13 @@ Ctx *current_ctx(int *status)
 
 using namespace raduls;
 
+// Host handle of a fitted model (device buffers of its own).
+struct raduls_model {
+    int device;
+    ModelBufs m;
+    u64 n;
+};
+
 extern "C" {
 
 int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
@@ -455,8 +667,8 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
         return rc;
     if (opts && opts->mode > 2u)
         return RADULS_ERR_INVALID_ARG;
-    if (opts && opts->mode == 2u)
-        return RADULS_ERR_UNSUPPORTED;
+    if (opts && opts->learned_log2_buckets && (opts->learned_log2_buckets < 12u || opts->learned_log2_buckets > 16u))
+        return RADULS_ERR_INVALID_ARG;
     if (opts && opts->stats)
         std::memset(opts->stats, 0, sizeof(raduls_stats));
     if (n_recs <= 1)
@@ -475,12 +687,170 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
     j.rw = rec_bytes / 8u;
     j.kw = key_bytes / 8u;
     j.stats = opts ? opts->stats : nullptr;
-    return run_sort(*c, j, (cudaStream_t)stream);
+    j.mode = opts ? opts->mode : 0u;
+    j.log2b = opts ? opts->learned_log2_buckets : 0u;
+    j.fallback_ratio = opts ? opts->fallback_ratio : 0.f;
+    j.train_steps = (opts && opts->train_steps) ? opts->train_steps : 100u;
+    return run_sort(*c, c->main, j, (cudaStream_t)stream);
 }
 
 int raduls_sort(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, void *stream)
 {
     return raduls_sort_ex(in, tmp, n_recs, rec_bytes, key_bytes, nullptr, stream);
+}
+
+int raduls_model_fit(raduls_model **out, const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                     uint32_t log2_buckets, uint32_t train_steps, void *stream)
+{
+    if (!out)
+        return RADULS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = check_args(in, in, 0, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n_recs < 2 || !in || log2_buckets < 12u || log2_buckets > 16u)
+        return RADULS_ERR_INVALID_ARG;
+    if ((uintptr_t)in & 15u)
+        return RADULS_ERR_MISALIGNED;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaError_t e = ctx_init(*c);
+    if (e != cudaSuccess)
+        return to_status(e);
+    cudaStream_t st = (cudaStream_t)stream;
+    raduls_model *m = new (std::nothrow) raduls_model();
+    if (!m)
+        return RADULS_ERR_OOM;
+    cudaGetDevice(&m->device);
+    m->n = n_recs;
+    // exact top-byte histogram of key word 0 (the root level)
+    u64 *root = nullptr;
+    e = cudaMalloc(&root, RADIX * 8);
+    if (e != cudaSuccess) {
+        delete m;
+        return RADULS_ERR_OOM;
+    }
+    SortJob hj{};
+    hj.in = (u64 *)in;
+    hj.tmp = (u64 *)in;
+    hj.n = n_recs;
+    hj.rw = rec_bytes / 8u;
+    hj.kw = key_bytes / 8u;
+    hj.digit = 8u * hj.kw - 1u;
+    hj.hist_out = root;
+    hj.mode = 1;
+    rc = run_sort(*c, c->main, hj, st);
+    Recorder rec;
+    rec.c = c;
+    rec.st = st;
+    // train_steps with the top bit set: warm start only, no Adam steps
+    const bool warm_only = (train_steps & 0x80000000u) != 0;
+    const u32 steps = warm_only ? 1u : train_steps;
+    if (!rc)
+        rc = model_fit(*c, m->m, (const u64 *)in, n_recs, rec_bytes / 8u, root, log2_buckets, steps, st, rec,
+                       warm_only);
+    cudaStreamSynchronize(st);
+    cudaFree(root);
+    if (rc) {
+        if (m->m.buf.p)
+            cudaFree(m->m.buf.p);
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return RADULS_OK;
+}
+
+int raduls_model_train(raduls_model *m, uint32_t stage, uint32_t steps, void *stream)
+{
+    if (!m || stage > 1u)
+        return RADULS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ModelBufs &M = m->m;
+    for (u32 k = 1; k <= steps; ++k) {
+        cudaError_t e = lm_launch_step(M.model, stage, M.theta, M.am, M.av, M.h, M.tot, M.E, M.G, M.Z, M.loss,
+                                       M.sample, M.seg_start, M.S, LEARN_RATE, (int)(M.steps_done + k), nullptr,
+                                       st);
+        if (e != cudaSuccess)
+            return to_status(e);
+    }
+    M.steps_done += steps;
+    return to_status(lm_launch_heights(M.model, M.theta, M.h, M.tot, M.E, M.G, M.Z, M.loss, st));
+}
+
+int raduls_model_loss_grad(raduls_model *m, uint32_t stage, double *h_loss, float *d_grad, void *stream)
+{
+    if (!m || !h_loss || !d_grad || stage > 1u)
+        return RADULS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    ModelBufs &M = m->m;
+    cudaError_t e = lm_launch_step(M.model, stage, M.theta, M.am, M.av, M.h, M.tot, M.E, M.G, M.Z, M.loss,
+                                   M.sample, M.seg_start, M.S, LEARN_RATE, 1, d_grad, st);
+    if (e != cudaSuccess)
+        return to_status(e);
+    double l = 0;
+    e = cudaMemcpyAsync(&l, M.loss, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    *h_loss = l / (double)M.S;
+    return to_status(e);
+}
+
+int raduls_model_buckets(const raduls_model *m, const uint64_t *d_keys, uint64_t n_keys, uint32_t *d_out,
+                         void *stream)
+{
+    if (!m || (n_keys && (!d_keys || !d_out)))
+        return RADULS_ERR_INVALID_ARG;
+    if (!n_keys)
+        return RADULS_OK;
+    return to_status(lm_launch_bucket(m->m.model, (const u64 *)d_keys, n_keys, d_out, (cudaStream_t)stream));
+}
+
+int raduls_model_sizes(const raduls_model *m, uint32_t *n_params, uint32_t *n_sample, uint32_t *log2_buckets)
+{
+    if (!m)
+        return RADULS_ERR_INVALID_ARG;
+    if (n_params)
+        *n_params = m->m.n_params_cap;
+    if (n_sample)
+        *n_sample = m->m.S;
+    if (log2_buckets)
+        *log2_buckets = m->m.log2b;
+    return RADULS_OK;
+}
+
+int raduls_model_copy_out(const raduls_model *m, uint64_t *h_root_counts, void *h_segments, float *h_theta,
+                          float *h_heights, uint64_t *h_sample, void *stream)
+{
+    if (!m)
+        return RADULS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ModelBufs &M = m->m;
+    cudaError_t e = cudaSuccess;
+    if (h_root_counts && e == cudaSuccess)
+        e = cudaMemcpyAsync(h_root_counts, M.model->root_cnt, RADIX * 8, cudaMemcpyDeviceToHost, st);
+    if (h_segments && e == cudaSuccess)
+        e = cudaMemcpyAsync(h_segments, M.model->seg, 2 * RADIX * sizeof(ModelSeg), cudaMemcpyDeviceToHost, st);
+    if (h_theta && e == cudaSuccess)
+        e = cudaMemcpyAsync(h_theta, M.theta, (size_t)M.n_params_cap * 4, cudaMemcpyDeviceToHost, st);
+    if (h_heights && e == cudaSuccess)
+        e = cudaMemcpyAsync(h_heights, M.h, (size_t)M.n_params_cap * 4, cudaMemcpyDeviceToHost, st);
+    if (h_sample && e == cudaSuccess)
+        e = cudaMemcpyAsync(h_sample, M.sample, (size_t)M.S * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    return to_status(e);
+}
+
+void raduls_model_free(raduls_model *m)
+{
+    if (!m)
+        return;
+    if (m->m.buf.p)
+        cudaFree(m->m.buf.p);
+    delete m;
 }
 
 int raduls_sort_batched(void *in, void *tmp, const uint64_t *d_seg_offsets, uint32_t n_segs, uint32_t rec_bytes,
@@ -527,7 +897,8 @@ int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32
     j.kw = key_bytes / 8u;
     j.digit = digit;
     j.hist_out = reinterpret_cast<u64 *>(d_hist_out);
-    return run_sort(*c, j, (cudaStream_t)stream);
+    j.mode = 1;
+    return run_sort(*c, c->main, j, (cudaStream_t)stream);
 }
 
 int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
@@ -559,7 +930,8 @@ int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_
     j.kw = key_bytes / 8u;
     j.digit = digit;
     j.single_pass = 1;
-    return run_sort(*c, j, (cudaStream_t)stream);
+    j.mode = 1;
+    return run_sort(*c, c->main, j, (cudaStream_t)stream);
 }
 
 int raduls_stream_status(void *stream)

@@ -26,12 +26,13 @@ u32 block_grid(const Shape &s);
 u32 copy_grid();
 
 cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items,
-                        const u32 *tile_item, u64 *hist, u64 *orand, Counters *ctrs, cudaStream_t st);
+                        const u32 *tile_item, u64 *hist, u64 *orand, u64 *dlight, Counters *ctrs,
+                        const Model *model, cudaStream_t st);
 cudaError_t launch_scatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
                            const u64 *bases, u64 *status, Counters *ctrs, u32 epoch, u64 wait_ns,
-                           u32 inject_tile, cudaStream_t st);
+                           u32 inject_tile, const Model *model, cudaStream_t st);
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks,
-                              Counters *ctrs, cudaStream_t st);
+                              Counters *ctrs, const u64 *seg_off, cudaStream_t st);
 
 // Planning kernels (plan.cu).
 struct PlanArgs {
@@ -50,16 +51,35 @@ struct PlanArgs {
     u32 key_words;
     u32 rw;
     u32 cap_b;
+    u32 warp_bin;     // sub-bins up to this size are sorted by one warp inside a run
     u32 tile_h, tile_s, tile_c;
     u32 single_pass;  // 1: distribute every item once, no children (single-step API)
+    u32 top_digit;    // most significant key digit (8 * key_words - 1)
 };
 
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
                         u32 cap_b, u32 tile_h, u32 force_grid, cudaStream_t st);
-cudaError_t launch_prep(u64 *hist, u64 *orand, const Counters *ctrs, u32 n_grid_hint, cudaStream_t st);
+cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint,
+                        cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,
                         Counters *ctrs, cudaStream_t st);
+
+// Learned model (learned.cu).
+cudaError_t lm_launch_sample(const u64 *in, u64 n, u32 rw, u32 S, u64 *out, cudaStream_t st);
+cudaError_t lm_launch_build(const u64 *sample, u32 S, u32 k_extra, const u64 *root_hist, u64 n, u32 log2b,
+                            const float *h, Model *M, u32 *seg_start, u32 max_knots, cudaStream_t st);
+cudaError_t lm_launch_init(float *theta, float *am, float *av, u32 n_params, cudaStream_t st);
+cudaError_t lm_launch_step(const Model *M, u32 stage, float *theta, float *am, float *av, float *h, float *tot,
+                           double *E, double *G, double *Z, double *loss, const u64 *sample, const u32 *seg_start,
+                           u32 S, float lr, int step, float *grad_out, cudaStream_t st);
+cudaError_t lm_launch_warm(const Model *M, u32 stage, const u64 *sample, const u32 *seg_start, float *theta,
+                           cudaStream_t st);
+cudaError_t lm_launch_heights(const Model *M, const float *theta, float *h, float *tot, double *E, double *G,
+                              double *Z, double *loss, cudaStream_t st);
+cudaError_t lm_launch_ratio(const u64 *dlight, Counters *ctrs, const Model *M, float limit, cudaStream_t st);
+cudaError_t lm_launch_heavy(const u64 *sample, u32 S, u32 thr, u64 *heavy, Model *M, cudaStream_t st);
+cudaError_t lm_launch_bucket(const Model *M, const u64 *keys, u64 n, u32 *out, cudaStream_t st);
 
 }  // namespace raduls

@@ -93,6 +93,18 @@ __device__ int next_varying_digit(u32 p, u64 vor, u64 vand)
     return (int)(p - (p % 8u)) - 1;
 }
 
+// Digit a sub-bin splits on next: the model's low digit after its top digit,
+// the key's top digit after the model's low digit, else the next key digit
+// down (-1 when none is left).
+__device__ __forceinline__ int child_digit(u32 p, u32 top)
+{
+    if (p == DIGIT_LEARNED_HI)
+        return (int)DIGIT_LEARNED_LO;
+    if (p == DIGIT_LEARNED_LO)
+        return (int)top;
+    return p > 0 ? (int)p - 1 : -1;
+}
+
 __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
 {
     __shared__ u64 s_cnt[RADIX];
@@ -105,13 +117,24 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
     for (u32 g = blockIdx.x; g < n_grid; g += gridDim.x) {
         const WorkItem it = a.grid_cur[g];
         const u32 p = it.digit;
+        const bool learned = p >= DIGIT_LEARNED_HI;
         const u64 h = a.hist[(u64)g * RADIX + d];
+        if (p == DIGIT_LEARNED_LO && !a.ctrs->learned_ok) {
+            // the learned partition failed its balance check: this bin goes on
+            // with plain key digits (its top-8-bit model split stays valid)
+            if (d == 0)
+                append_grid(a, it.begin, it.count, a.top_digit, it.flags);
+            __syncthreads();
+            continue;
+        }
         const int is_const = __syncthreads_or(h == it.count);
         if (is_const && !a.single_pass) {
             if (d == 0) {
-                const int np = next_varying_digit(p, a.orand[2ull * g], a.orand[2ull * g + 1]);
+                const int np = learned ? child_digit(p, a.top_digit)
+                                       : next_varying_digit(p, a.orand[2ull * g], a.orand[2ull * g + 1]);
                 if (np >= 0) {
-                    atomicAdd(&a.ctrs->skipped, (u64)(p - (u32)np));
+                    if (!learned)
+                        atomicAdd(&a.ctrs->skipped, (u64)(p - (u32)np));
                     append_grid(a, it.begin, it.count, (u32)np, it.flags);
                 } else {
                     atomicAdd(&a.ctrs->skipped, (u64)(p + 1));
@@ -167,29 +190,40 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
         }
         const u32 cflags = it.flags ^ ITEM_IN_TMP;
         const bool big = h > a.cap_b;
+        const int cd = child_digit(p, a.top_digit);
         s_big[d] = big ? 1 : 0;
         if (big) {
-            if (p > 0)
-                append_grid(a, it.begin + ex, h, p - 1, cflags);
+            if (cd >= 0)
+                append_grid(a, it.begin + ex, h, (u32)cd, cflags);
             else if (cflags & ITEM_IN_TMP)
                 append_copy(a, it.begin + ex, h);
         }
         __syncthreads();
-        if (d == 0) {
-            // pack consecutive small sub-bins into runs of at most cap_b records
+        if (d == 0 && learned) {
+            // sub-bins of a model split share no known key digit: each is sorted on
+            // its own by the whole key
+            for (u32 c = 0; c < RADIX; ++c)
+                if (!s_big[c] && s_cnt[c] > 0)
+                    append_block(a, s_ex[c], s_cnt[c], a.top_digit, cflags);
+        } else if (d == 0) {
+            // small sub-bins: up to WARP_BIN records -> packed into runs of at most
+            // cap_b records (one warp per sub-bin); bigger ones -> one item each
+            const u32 cdigit = cd >= 0 ? (u32)cd : 0u;
             u64 acc_b = 0, acc_n = 0;
             for (u32 c = 0; c < RADIX; ++c) {
                 const u64 n = s_cnt[c];
-                if (s_big[c]) {
+                if (s_big[c] || n > a.warp_bin) {
                     if (acc_n)
-                        append_block(a, acc_b, acc_n, p, cflags);
+                        append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
                     acc_n = 0;
+                    if (!s_big[c])
+                        append_block(a, s_ex[c], n, cdigit, cflags);
                     continue;
                 }
                 if (n == 0)
                     continue;
                 if (acc_n && acc_n + n > a.cap_b) {
-                    append_block(a, acc_b, acc_n, p, cflags);
+                    append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
                     acc_n = 0;
                 }
                 if (acc_n == 0)
@@ -197,7 +231,7 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
                 acc_n += n;
             }
             if (acc_n)
-                append_block(a, acc_b, acc_n, p, cflags);
+                append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
         }
         __syncthreads();
     }
@@ -227,12 +261,14 @@ __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u
         tile_hist[j] = 0;
 }
 
-__global__ void prep_kernel(u64 *hist, u64 *orand, const Counters *ctrs)
+__global__ void prep_kernel(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs)
 {
     const u64 rows = ctrs->grid_cur;
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows * RADIX; i += stride)
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows * RADIX; i += stride) {
         hist[i] = 0;
+        dlight[i] = 0;
+    }
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
         orand[2 * i] = 0;
         orand[2 * i + 1] = ~0ull;
@@ -287,12 +323,12 @@ cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(u64 *hist, u64 *orand, const Counters *ctrs, u32 n_grid_hint, cudaStream_t st)
+cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, cudaStream_t st)
 {
     u64 work = (u64)n_grid_hint * RADIX;
     u64 want = (work + 255) / 256 + 1;
     u32 blocks = (u32)(want < 4096ull ? want : 4096ull);
-    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, ctrs);
+    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, dlight, ctrs);
     return cudaGetLastError();
 }
 

@@ -39,5 +39,6 @@ def gpu_sort(recs: np.ndarray, key_bytes: int, **kw) -> np.ndarray:
         p.raduls_sort_ex(d, t, n, rw * 8, key_bytes, **kw)
     else:
         p.raduls_sort(d, t, n, rw * 8, key_bytes)
-    assert p.raduls_stream_status() == 0
+    st = p.raduls_stream_status()
+    assert st == 0, f"device status {st} ({p.raduls_status_string(st)})"
     return from_dev(d, n, rw)
