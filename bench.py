@@ -45,12 +45,17 @@ UNIT = "records/s"
 
 WORKLOADS = {
     "uniform16": dict(desc="2^31 records x 16 B (u64 key uniform over 2^64 + u64 index payload), plain MSD sort",
-                      n=1 << 31, rec=16, key=8),
-    "uniform8": dict(desc="2^20 records x 8 B (u64 key only, uniform), plain MSD sort", n=1 << 20, rec=8, key=8),
-    "skewed16": dict(desc="2^30 records x 16 B, Zipf(1.1)/exponential/normal key mixture, plain MSD sort",
-                     n=1 << 30, rec=16, key=8),
-    "widekey32": dict(desc="2^28 records x 32 B, 16-byte key (Zipf(1.0) high word, uniform low word)",
-                      n=1 << 28, rec=32, key=16),
+                      n=1 << 31, rec=16, key=8, mode="plain"),
+    "uniform8": dict(desc="2^20 records x 8 B (u64 key only, uniform), plain MSD sort", n=1 << 20, rec=8, key=8,
+                     mode="plain"),
+    "skewed16": dict(desc="2^30 records x 16 B, Zipf(1.1)/exponential/normal key mixture; learned first "
+                          "partition (plain MSD timed alongside)", n=1 << 30, rec=16, key=8, mode="learned"),
+    "widekey32": dict(desc="2^28 records x 32 B, 16-byte key (Zipf(1.0) high word over 2^20 values, uniform low "
+                           "word); learned first partition (plain MSD timed alongside)", n=1 << 28, rec=32, key=16,
+                      mode="learned"),
+    "batched16": dict(desc="200,000 arrays of 16 B records, sizes log-uniform on [16, 42324] (expected total "
+                           "2^30), odd arrays with a fixed top half-key; one batched call (a per-array plain loop "
+                           "on a prefix of the arrays timed alongside)", n=0, rec=16, key=8, mode="batched"),
 }
 
 # ncu DRAM traffic of one distribution launch, per record moved, measured on
@@ -128,39 +133,64 @@ class ClockSampler:
 
 
 def make_input(name: str, n: int):
-    """Pinned host records of the workload (uint64, (n, rec/8))."""
+    """Pinned host records of the workload (uint64, (n, rec/8)), and the array
+    offsets for the batched workload (else None)."""
     import torch
     w = WORKLOADS[name]
     rw = w["rec"] // 8
+    offsets = None
+    if name == "batched16":
+        recs, offsets = datagen.batched16()
+        n = recs.shape[0]
     host = torch.empty((n, rw), dtype=torch.int64, pin_memory=True)
     arr = host.numpy().view(np.uint64)
-    gen = getattr(datagen, name)
-    if name == "uniform8":
-        arr[:] = gen(n)
+    if name == "batched16":
+        arr[:] = recs
+        del recs
+    elif name == "uniform8":
+        arr[:] = datagen.uniform8(n)
     else:
-        gen(n, out=arr)
-    return host
+        getattr(datagen, name)(n, out=arr)
+    return host, offsets
+
+
+def _prefix(name: str, m: int):
+    """About m leading records of the workload, and for the batched workload
+    the offsets of the whole arrays they hold (else None)."""
+    if name == "batched16":
+        sizes = datagen.batched_sizes()
+        cut = int(np.searchsorted(np.cumsum(sizes), m)) + 1
+        return datagen.batched16(sizes=sizes[:cut])
+    return getattr(datagen, name)(m), None
+
+
+def _oracle_run(oracle, recs, offs, key, cores):
+    if offs is None:
+        oracle.sort(recs, key, threads=cores)
+    else:
+        oracle.sort_segments(recs, key, offs, threads=cores)
 
 
 def cpu_baseline(name: str, budget_s: float = 15.0) -> dict:
-    """The oracle, as it stands, on a bounded prefix of the workload."""
+    """The oracle, as it stands, on a bounded prefix of the workload (whole
+    records sorted by the LSD counting sort; for the batched workload the
+    prefix's arrays sorted one by one)."""
     import oracle
     w = WORKLOADS[name]
     cores = oracle.usable_cores()
     m = 1 << 22
-    gen = getattr(datagen, name)
-    recs = gen(m) if name == "uniform8" else gen(m)
+    recs, offs = _prefix(name, m)
     t0 = time.perf_counter()
-    oracle.sort(recs, w["key"], threads=cores)
+    _oracle_run(oracle, recs, offs, w["key"], cores)
     dt = time.perf_counter() - t0
     target = int(m * budget_s / max(dt, 1e-3))
-    m2 = max(m, min(1 << 28, w["n"], 1 << int(np.log2(max(target, 1)))))
+    m2 = max(m, min(1 << 28, w["n"] or (1 << 30), 1 << int(np.log2(max(target, 1)))))
     if m2 > m:
-        recs = gen(m2)
+        recs, offs = _prefix(name, m2)
         t0 = time.perf_counter()
-        oracle.sort(recs, w["key"], threads=cores)
+        _oracle_run(oracle, recs, offs, w["key"], cores)
         dt = time.perf_counter() - t0
-        m = m2
+    m = recs.shape[0]
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {m} records of the {name} workload ({w['rec']} B records), one LSD oracle sort "
                       f"with {cores} threads, {dt:.2f} s"}
@@ -173,15 +203,15 @@ def run_reference(args, rank: int, world: int) -> None:
     import oracle
     w = WORKLOADS[args.workload]
     cores = oracle.usable_cores()
-    gen = getattr(datagen, args.workload)
     m = args.ref_records or (1 << 24)
-    recs = gen(m)
+    recs, offs = _prefix(args.workload, m)
+    m = recs.shape[0]
     for _ in range(args.warmup):
-        oracle.sort(recs, w["key"], threads=cores)
+        _oracle_run(oracle, recs, offs, w["key"], cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sort(recs, w["key"], threads=cores)
+        _oracle_run(oracle, recs, offs, w["key"], cores)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = m * args.steps / tot
@@ -250,30 +280,40 @@ def main():
     pkg.load()
 
     w = WORKLOADS[args.workload]
-    n = args.records or w["n"]
+    mode = w["mode"]
     rec, key = w["rec"], w["key"]
     rw = rec // 8
-
-    host_in = make_input(args.workload, n)
+    host_in, offsets = make_input(args.workload, args.records or w["n"])
+    n = host_in.shape[0]
     pristine = host_in.to("cuda", non_blocking=False)
     recs = torch.empty_like(pristine)
     tmp = torch.empty_like(pristine)
+    d_off = None
+    if offsets is not None:
+        d_off = torch.from_numpy(offsets.view(np.int64)).cuda()
     stream = torch.cuda.current_stream()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
+    def one_sort(stats=False, how=None):
+        how = how or mode
+        if how == "batched":
+            pkg.raduls_sort_batched(recs, tmp, d_off, offsets.size - 1, rec, key)
+            return None
+        return pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode=how, stats=stats)
+
     # warm-up (untimed), first one checked
     for i in range(args.warmup):
         recs.copy_(pristine)
-        pkg.raduls_sort(recs, tmp, n, rec, key)
+        one_sort()
         if i == 0:
             torch.cuda.synchronize()
             st = pkg.raduls_stream_status()
             if st != 0:
                 raise SystemExit(f"device status {st} during warm-up")
-            if rec >= 16 and key == 8:
+            if rec == 16 and key == 8 and mode != "batched":
                 assert check_sorted_gpu(recs, pristine[:, 0]), "warm-up sort output is not the stable order"
 
     hbm_peak, peak_kind = peaks()
@@ -285,6 +325,7 @@ def main():
     launches = 0
     total_bytes = 0
     kernel_ms = {}
+    learned_info = None
     for _ in range(args.steps):
         recs.copy_(pristine)                      # restore the input (untimed)
         barrier()
@@ -292,11 +333,13 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        st = pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode="plain", stats=True)
+        st = one_sort(stats=True)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
         step_ms.append(ev0.elapsed_time(ev1))
+        if st is None:
+            continue
         scat_ms += st["kernel_ms"]["scatter"]
         scat_launches += st["kernel_launches"]["scatter"]
         scat_bytes += st["scatter_bytes"]
@@ -304,6 +347,9 @@ def main():
         total_bytes += st["hist_bytes_read"] + st["scatter_bytes"] + st["block_bytes"]
         for k, v in st["kernel_ms"].items():
             kernel_ms[k] = kernel_ms.get(k, 0.0) + v
+        if st.get("learned_used"):
+            learned_info = {"learned_used": st["learned_used"], "fell_back": st["learned_fell_back"],
+                            "max_over_ideal_bucket": st["learned_ratio"]}
     clocks = sampler.stop()
     if pkg.raduls_stream_status() != 0:
         raise SystemExit("device-side error during the timed steps")
@@ -314,6 +360,45 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
     value = n * world * args.steps / (tot_ms / 1e3)
+
+    # the same input through the plain path (learned workloads) or a per-array
+    # plain loop over a prefix of the arrays (batched workload), for comparison
+    comparison = None
+    if mode == "learned":
+        cms = []
+        for _ in range(max(2, args.steps // 2)):
+            recs.copy_(pristine)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cst = one_sort(stats=True, how="plain")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cms.append(e0.elapsed_time(e1))
+        comparison = {"plain_records_per_s": n * len(cms) / (sum(cms) / 1e3),
+                      "plain_ms_per_step": sum(cms) / len(cms),
+                      "plain_bytes_moved": cst["hist_bytes_read"] + cst["scatter_bytes"] + cst["block_bytes"],
+                      "learned_bytes_moved": total_bytes // max(args.steps, 1),
+                      "learned_speedup": (sum(cms) / len(cms)) / (tot_ms / args.steps)}
+    elif mode == "batched":
+        k_arrays = min(2000, offsets.size - 1)
+        lo, hi = int(offsets[0]), int(offsets[k_arrays])
+        recs.copy_(pristine)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for a in range(k_arrays):
+            s0, s1 = int(offsets[a]), int(offsets[a + 1])
+            if s1 - s0 > 1:
+                pkg.raduls_sort(recs[s0:s1], tmp[s0:s1], s1 - s0, rec, key)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms = e0.elapsed_time(e1)
+        comparison = {"per_array_plain_loop_records_per_s": (hi - lo) / (loop_ms / 1e3),
+                      "loop_sample": f"first {k_arrays} arrays ({hi - lo} records) sorted one raduls_sort call each",
+                      "batched_speedup": ((hi - lo) / (loop_ms / 1e3)) and value / ((hi - lo) / (loop_ms / 1e3))}
 
     # end to end: pinned host records -> device -> sort -> device -> pinned host
     e2e = None
@@ -327,7 +412,7 @@ def main():
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             recs.copy_(host_in, non_blocking=True)
-            pkg.raduls_sort(recs, tmp, n, rec, key)
+            one_sort()
             host_out.copy_(recs, non_blocking=True)
             ev1.record(stream)
             torch.cuda.synchronize()
@@ -363,7 +448,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "n_records": n, "rec_bytes": rec,
-                   "key_bytes": key, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "key_bytes": key, "mode": mode,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "input 32 GiB-class, far larger than L2; restored from a pristine device copy before each step"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -371,6 +457,10 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if comparison is not None:
+        line["comparison"] = comparison
+    if learned_info is not None:
+        line["learned"] = learned_info
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -23,6 +23,7 @@ constexpr u32 FULL_MASK = 0xffffffffu;
 // Status codes shared with the C ABI (raduls.h).
 enum : u32 {
     ST_OK = 0,
+    ST_BAD_ARG = 1,
     ST_TIMEOUT = 6,
     ST_INTERNAL = 7,
 };

@@ -70,8 +70,8 @@ struct DevBuf {
 struct Work {
     Counters *ctrs = nullptr;    // device
     Counters *h_ctrs = nullptr;  // pinned host mirror
+    u32 *epoch = nullptr;        // device: look-back epoch of the last distribution launch, wrap flag
     DevBuf lists, hist, status, tiles;
-    u32 epoch = 0;
 };
 
 // Device buffers of one learned model (see the Model struct in common.cuh).
@@ -187,6 +187,12 @@ cudaError_t work_init(Work &w)
     cudaError_t e = cudaMalloc(&w.ctrs, sizeof(Counters));
     if (e != cudaSuccess)
         return e;
+    e = cudaMalloc(&w.epoch, 16);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemset(w.epoch, 0, 16);
+    if (e != cudaSuccess)
+        return e;
     e = cudaMemset(w.ctrs, 0, sizeof(Counters));
     if (e != cudaSuccess)
         return e;
@@ -279,8 +285,11 @@ cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B
     e = ensure(wk.status, st_tiles * RADIX * 8, true, &grew, st);
     if (e != cudaSuccess)
         return e;
-    if (grew)
-        wk.epoch = 0;
+    if (grew) {  // fresh zeroed words: restart the epochs
+        e = cudaMemsetAsync(wk.epoch, 0, 16, st);
+        if (e != cudaSuccess)
+            return e;
+    }
     e = ensure(wk.tiles, st_tiles * 4, false);
     if (e != cudaSuccess)
         return e;
@@ -290,16 +299,6 @@ cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B
     if ((u64)caps.scat_tiles * 4 > wk.tiles.bytes)
         caps.scat_tiles = (u32)(wk.tiles.bytes / 4);
     return cudaSuccess;
-}
-
-u32 next_epoch(Work &wk, cudaStream_t st)
-{
-    wk.epoch += 1;
-    if (wk.epoch >= LB_EPOCH_MASK) {
-        cudaMemsetAsync(wk.status.p, 0, wk.status.bytes, st);
-        wk.epoch = 1;
-    }
-    return wk.epoch;
 }
 
 // Times each launch with a pair of CUDA events on the launching stream when
@@ -582,9 +581,9 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         a.single_pass = j.single_pass ? 1u : 0u;
         a.top_digit = top;
         TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-        const u32 epoch = next_epoch(wk, st);
+        TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
         TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs,
-                                               epoch, c.wait_ns, c.inject_tile, model, st));
+                                               wk.epoch, c.wait_ns, c.inject_tile, model, st));
         c.inject_tile = ~0u;
         TIMED(RADULS_K_SETUP, launch_advance(wk.ctrs, st));
         if (j.single_pass)
@@ -630,6 +629,124 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             o.kernel_ms[rec.cls[i]] += ms;
         }
     }
+    return RADULS_OK;
+}
+
+// ------------------------------------------------------------ batched sort
+//
+// Many independent arrays in one call.  The arrays are classified on the
+// device; then a fixed sequence of MSD levels (8 per key word: each level
+// splits or skips at least one digit of every big bin) runs without any host
+// round trip -- every kernel reads its work counts from device memory and
+// returns at once when a level has nothing left -- followed by the copy-back
+// and the on-chip sorts.  The whole sequence is captured once into a CUDA
+// graph per (buffers, offsets, shape) and replayed by later calls.
+
+struct BatchGraph {
+    cudaStream_t cap = nullptr;  // library stream the graph is captured on
+    cudaGraphExec_t exec = nullptr;
+    void *in = nullptr, *tmp = nullptr;
+    const void *off = nullptr;
+    u64 n = 0;
+    u32 n_segs = 0, rw = 0, kw = 0;
+};
+
+BatchGraph g_batch[MAX_DEVICES];
+
+int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, u64 n, u32 rw,
+                    u32 kw, Lists &L, LevelBufs &B, cudaStream_t st)
+{
+    const u32 top = 8u * kw - 1u;
+    CK(launch_batched_init(off, n_segs, L.grid[0], L.blocks, L.tile_hist, wk.ctrs, L.caps, top, s.cap_b, s.tile_h,
+                           st));
+    int cur = 0;
+    const u32 levels = 8u * kw;
+    for (u32 level = 0; level < levels; ++level) {
+        CK(launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, L.caps.grid, st));
+        CK(launch_hist(s, in, tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight, wk.ctrs, nullptr, st));
+        PlanArgs a{};
+        a.grid_cur = L.grid[cur];
+        a.grid_next = L.grid[cur ^ 1];
+        a.scat = L.scat;
+        a.blocks = L.blocks;
+        a.copies = L.copies;
+        a.hist = B.hist;
+        a.orand = B.orand;
+        a.tile_hist = L.tile_hist;
+        a.tile_scat = B.tile_scat;
+        a.tile_copy = L.tile_copy;
+        a.ctrs = wk.ctrs;
+        a.caps = L.caps;
+        a.key_words = kw;
+        a.rw = rw;
+        a.cap_b = s.cap_b;
+        a.warp_bin = WARP_BIN;
+        a.tile_h = s.tile_h;
+        a.tile_s = s.tile_s;
+        a.tile_c = s.tile_c;
+        a.single_pass = 0;
+        a.top_digit = top;
+        CK(launch_plan(a, 0, st));
+        CK(launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+        CK(launch_scatter(s, in, tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs, wk.epoch, c.wait_ns, ~0u,
+                          nullptr, st));
+        CK(launch_advance(wk.ctrs, st));
+        cur ^= 1;
+    }
+    CK(launch_copy(s, in, tmp, L.copies, L.tile_copy, wk.ctrs, st));
+    CK(launch_block_sort(s, in, tmp, L.blocks, wk.ctrs, off, st));
+    fold_status_kernel<<<1, 1, 0, st>>>(wk.ctrs, c.dev_status);
+    CK(cudaGetLastError());
+    return RADULS_OK;
+}
+
+int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, u64 n, u32 rw, u32 kw,
+                cudaStream_t st)
+{
+    Work &wk = c.main;
+    const Shape s = choose_shape(rw, kw);
+    Lists L{};
+    // the batched init adds up to n_segs on-chip items and (n / cap_b) runs to the usual bounds
+    CK(work_lists(wk, s, n + 2ull * n_segs + 2ull * s.cap_b, L));
+    LevelBufs B{};
+    CK(work_level(wk, s, n, L.caps.grid, B, L.caps, st));
+    {
+        std::lock_guard<std::mutex> g(g_setting_mu);
+        c.wait_ns = g_wait_ns;
+    }
+    BatchGraph &bg = g_batch[dev];
+    const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
+                     bg.rw == rw && bg.kw == kw && bg.in != nullptr;
+    if (!hit) {
+        if (bg.exec) {
+            cudaGraphExecDestroy(bg.exec);
+            bg.exec = nullptr;
+        }
+        // buffers must be sized before the capture: nothing may allocate inside it.
+        // The caller's stream may be the legacy default stream, which cannot be
+        // captured: capture on a stream of our own, launch on the caller's.
+        CK(cudaStreamSynchronize(st));
+        if (!bg.cap)
+            CK(cudaStreamCreateWithFlags(&bg.cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(bg.cap, cudaStreamCaptureModeRelaxed));
+        int rc = enqueue_batched(c, wk, s, in, tmp, off, n_segs, n, rw, kw, L, B, bg.cap);
+        cudaError_t e = cudaStreamEndCapture(bg.cap, &graph);
+        if (rc)
+            return rc;
+        CK(e);
+        e = cudaGraphInstantiate(&bg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        bg.in = in;
+        bg.tmp = tmp;
+        bg.off = off;
+        bg.n = n;
+        bg.n_segs = n_segs;
+        bg.rw = rw;
+        bg.kw = kw;
+    }
+    CK(cudaGraphLaunch(bg.exec, st));
     return RADULS_OK;
 }
 
@@ -856,14 +973,39 @@ void raduls_model_free(raduls_model *m)
 int raduls_sort_batched(void *in, void *tmp, const uint64_t *d_seg_offsets, uint32_t n_segs, uint32_t rec_bytes,
                         uint32_t key_bytes, void *stream)
 {
-    (void)in;
-    (void)tmp;
-    (void)d_seg_offsets;
-    (void)n_segs;
-    (void)rec_bytes;
-    (void)key_bytes;
-    (void)stream;
-    return RADULS_ERR_UNSUPPORTED;
+    int rc = check_args(in, tmp, 0, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n_segs == 0)
+        return RADULS_OK;
+    if (!d_seg_offsets || !in || !tmp)
+        return RADULS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_seg_offsets & 7u) || ((uintptr_t)in & 15u) || ((uintptr_t)tmp & 15u))
+        return RADULS_ERR_MISALIGNED;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    // the total record count sizes the workspace: read the last offset
+    u64 n = 0;
+    cudaError_t e = cudaMemcpyAsync(&n, d_seg_offsets + n_segs, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return to_status(e);
+    rc = check_args(in, tmp, n, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n <= 1)
+        return RADULS_OK;
+    std::lock_guard<std::mutex> g(c->mu);
+    e = ctx_init(*c);
+    if (e != cudaSuccess)
+        return to_status(e);
+    return run_batched(*c, dev, (u64 *)in, (u64 *)tmp, (const u64 *)d_seg_offsets, n_segs, n, rec_bytes / 8u,
+                       key_bytes / 8u, st);
 }
 
 int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, uint32_t digit,

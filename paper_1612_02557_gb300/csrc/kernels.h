@@ -29,7 +29,7 @@ cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const Wor
                         const u32 *tile_item, u64 *hist, u64 *orand, u64 *dlight, Counters *ctrs,
                         const Model *model, cudaStream_t st);
 cudaError_t launch_scatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                           const u64 *bases, u64 *status, Counters *ctrs, u32 epoch, u64 wait_ns,
+                           const u64 *bases, u64 *status, Counters *ctrs, const u32 *epoch, u64 wait_ns,
                            u32 inject_tile, const Model *model, cudaStream_t st);
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks,
                               Counters *ctrs, const u64 *seg_off, cudaStream_t st);
@@ -63,6 +63,9 @@ cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs
                         cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
+cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
+                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, cudaStream_t st);
+cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st);
 cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,
                         Counters *ctrs, cudaStream_t st);
 

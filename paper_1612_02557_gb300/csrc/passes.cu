@@ -183,8 +183,8 @@ template <int THREADS, int K, int RW>
 __global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 2 : 4)
 scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__restrict__ items,
                const u32 *__restrict__ tile_item, const u64 *__restrict__ bases, u64 *__restrict__ status,
-               Counters *__restrict__ ctrs, u32 rw_rt, u32 key_words, u32 epoch, u64 wait_ns, u32 inject_tile,
-               const Model *__restrict__ model)
+               Counters *__restrict__ ctrs, u32 rw_rt, u32 key_words, const u32 *__restrict__ epoch, u64 wait_ns,
+               u32 inject_tile, const Model *__restrict__ model)
 {
     constexpr u32 TILE = THREADS * K;
     static_assert(TILE <= 65536, "tile slots are 16-bit");
@@ -195,7 +195,7 @@ scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__re
     const u32 rw = RW ? (u32)RW : rw_rt;
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     const u32 n_tiles = ctrs->scatter_tiles;
-    const u32 ep = epoch & LB_EPOCH_MASK;
+    const u32 ep = *epoch & LB_EPOCH_MASK;
 
     for (;;) {
         if (tid == 0) {
@@ -369,8 +369,8 @@ cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const Wor
 }
 
 cudaError_t launch_scatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                           const u64 *bases, u64 *status, Counters *ctrs, u32 epoch, u64 wait_ns, u32 inject_tile,
-                           const Model *model, cudaStream_t st)
+                           const u64 *bases, u64 *status, Counters *ctrs, const u32 *epoch, u64 wait_ns,
+                           u32 inject_tile, const Model *model, cudaStream_t st)
 {
     const u32 grid = scatter_grid(s);
     switch (s.scat_var) {

@@ -316,6 +316,114 @@ copy_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *_
     }
 }
 
+// ------------------------------------------------------------ batched sort
+
+__global__ void batched_reset_kernel(Counters *ctrs)
+{
+    Counters c = {};
+    *ctrs = c;
+}
+
+// Offsets must start at 0 and never decrease; otherwise nothing is sorted.
+__global__ void batched_validate_kernel(const u64 *__restrict__ off, u32 n_segs, Counters *ctrs)
+{
+    for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x)
+        if (off[s + 1] < off[s] || (s == 0 && off[0] != 0))
+            set_error(ctrs, ST_BAD_ARG);
+}
+
+// Classify every array by size: bigger than cap_b -> first grid list (its top
+// key digit); bigger than warp_bin -> one on-chip item; otherwise -> a run of
+// consecutive small arrays whose starts share a window of `win` records and
+// whose indices share a block of 256 (so a run holds < cap_b records and at
+// most 256 arrays), sorted one warp per array.
+__global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs, WorkItem *grid0, WorkItem *blocks,
+                                        u32 *tile_hist, Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 warp_bin,
+                                        u32 tile_h, u32 win)
+{
+    if (ctrs->err)
+        return;
+    auto small = [&](u32 s) { return off[s + 1] - off[s] <= warp_bin; };
+    auto key = [&](u32 s) { return (off[s] / win) * 1048576ull + (s >> 8); };
+    for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x) {
+        const u64 a = off[s], c = off[s + 1] - a;
+        if (c > cap_b) {
+            const u32 slot = atomicAdd(&ctrs->grid_cur, 1u);
+            const u32 nt = (u32)((c + tile_h - 1) / tile_h);
+            const u32 tb = atomicAdd(&ctrs->grid_cur_tiles, nt);
+            if (slot >= caps.grid || (u64)tb + nt > caps.hist_tiles) {
+                set_error(ctrs, ST_INTERNAL);
+                continue;
+            }
+            WorkItem it = {a, c, top, 0u, tb, slot};
+            grid0[slot] = it;
+            for (u32 t = 0; t < nt; ++t)
+                tile_hist[tb + t] = slot;
+        } else if (c > warp_bin) {
+            const u64 slot = atomicAdd(&ctrs->block, 1ull);
+            if (slot >= caps.block) {
+                set_error(ctrs, ST_INTERNAL);
+                continue;
+            }
+            WorkItem it = {a, c, top, 0u, 0u, 0u};
+            blocks[slot] = it;
+        } else if (s == 0 || !small(s - 1) || key(s - 1) != key(s)) {
+            u32 e = s + 1;
+            while (e < n_segs && small(e) && key(e) == key(s))
+                ++e;
+            const u64 total = off[e] - a;
+            if (total > 1) {
+                const u64 slot = atomicAdd(&ctrs->block, 1ull);
+                if (slot >= caps.block) {
+                    set_error(ctrs, ST_INTERNAL);
+                    continue;
+                }
+                WorkItem it = {a, total, top, ITEM_RUN | ITEM_SEG, s, e - s};
+                blocks[slot] = it;
+            }
+        }
+    }
+}
+
+cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
+                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, cudaStream_t st)
+{
+    batched_reset_kernel<<<1, 1, 0, st>>>(ctrs);
+    const u32 blocks_n = n_segs / 256 + 1 < 4096 ? n_segs / 256 + 1 : 4096;
+    batched_validate_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, ctrs);
+    batched_classify_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, grid0, blocks, tile_hist, ctrs, caps, top, cap_b,
+                                                      WARP_BIN, tile_h, cap_b - WARP_BIN);
+    return cudaGetLastError();
+}
+
+// Look-back epoch held on the device: the next distribution launch's epoch.
+// When it would wrap, the status words are cleared first (wrap flag ep[1]).
+__global__ void epoch_next_kernel(u32 *ep)
+{
+    u32 e = ep[0] + 1u;
+    ep[1] = 0;
+    if (e >= LB_EPOCH_MASK) {
+        e = 1;
+        ep[1] = 1;
+    }
+    ep[0] = e;
+}
+
+__global__ void status_clear_kernel(const u32 *ep, u64 *status, u64 words)
+{
+    if (!ep[1])
+        return;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (u64)gridDim.x * blockDim.x)
+        status[i] = 0;
+}
+
+cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st)
+{
+    epoch_next_kernel<<<1, 1, 0, st>>>(ep);
+    status_clear_kernel<<<1024, 256, 0, st>>>(ep, status, words);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
                         u32 cap_b, u32 tile_h, u32 force_grid, cudaStream_t st)
 {
@@ -334,9 +442,8 @@ cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs
 
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st)
 {
-    u32 blocks = n_grid < 65535u ? n_grid : 65535u;
-    if (blocks == 0)
-        blocks = 1;
+    // n_grid == 0: count unknown on the host (device-driven levels): a fixed grid loops
+    u32 blocks = n_grid == 0 ? 1216u : (n_grid < 65535u ? n_grid : 65535u);
     plan_kernel<<<blocks, RADIX, 0, st>>>(a);
     return cudaGetLastError();
 }

@@ -1,0 +1,88 @@
+"""GPU parity of the batched (segmented) sort: every array equals the oracle's
+sort of that array on its own; records never cross arrays."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import datagen
+from gpu_util import from_dev, lib, scratch, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib()
+
+
+def _run(recs, offsets, key_bytes, repeat=1):
+    import torch
+    p = lib()
+    n, rw = recs.shape
+    d_off = torch.from_numpy(offsets.astype(np.uint64).view(np.int64)).cuda()
+    t = scratch(n, rw)
+    out = None
+    for _ in range(repeat):
+        d = to_dev(recs)
+        p.raduls_sort_batched(d, t, d_off, offsets.size - 1, rw * 8, key_bytes)
+        st = p.raduls_stream_status()
+        assert st == 0, f"device status {st}"
+        got = from_dev(d, n, rw)
+        assert out is None or np.array_equal(out, got)
+        out = got
+    return out
+
+
+def _check(oracle_mod, recs, offsets, key_bytes, repeat=1):
+    got = _run(recs, offsets, key_bytes, repeat)
+    np.testing.assert_array_equal(got, oracle_mod.sort_segments(recs, key_bytes, offsets, threads=8))
+
+
+def test_workload_sizes_mixed(oracle_mod):
+    """1500 arrays, sizes log-uniform on [16, 42324], odd arrays with a fixed top half-key."""
+    sizes = datagen.batched_sizes(1500)
+    recs, offs = datagen.batched16(sizes=sizes)
+    _check(oracle_mod, recs, offs, 8, repeat=2)   # the second call replays the captured graph
+
+
+def test_every_size_class_and_edges(oracle_mod):
+    rng = np.random.default_rng(3)
+    sizes = np.array([0, 1, 2, 0, 3, 31, 32, 33, 255, 256, 257, 1000, 4095, 4096, 4097, 8191, 9000,
+                      70000, 0, 1, 5, 300001, 2, 2, 2] + list(rng.integers(0, 300, size=600)), dtype=np.int64)
+    recs, offs = datagen.batched16(sizes=sizes)
+    _check(oracle_mod, recs, offs, 8)
+
+
+def test_many_tiny_arrays(oracle_mod):
+    sizes = np.random.default_rng(4).integers(0, 8, size=20000)
+    recs, offs = datagen.batched16(sizes=sizes)
+    _check(oracle_mod, recs, offs, 8)
+
+
+def test_wide_records_and_keys(oracle_mod):
+    for rec_bytes, key_bytes in ((32, 16), (24, 8), (8, 8)):
+        sizes = np.random.default_rng(rec_bytes).integers(0, 6000, size=120)
+        n = int(sizes.sum())
+        recs = datagen.random_records(n, rec_bytes, key_bytes, rec_bytes, alphabet=None)
+        if rec_bytes == 32:
+            recs[:, 0] &= np.uint64(0xFF)          # heavy duplicates in the top word
+        offs = np.zeros(sizes.size + 1, dtype=np.uint64)
+        np.cumsum(sizes, out=offs[1:])
+        _check(oracle_mod, recs, offs, key_bytes)
+
+
+def test_bad_offsets_are_reported_and_nothing_moves():
+    import torch
+    p = lib()
+    recs = datagen.random_records(1000, 16, 8, 1)
+    offs = np.array([0, 600, 300, 1000], dtype=np.uint64)   # decreasing
+    d = to_dev(recs)
+    t = scratch(1000, 2)
+    d_off = torch.from_numpy(offs.view(np.int64)).cuda()
+    p.raduls_sort_batched(d, t, d_off, 3, 16, 8)
+    assert p.raduls_stream_status() == 1
+    np.testing.assert_array_equal(from_dev(d, 1000, 2), recs)
