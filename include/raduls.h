@@ -191,6 +191,26 @@ int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32
 int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_t rec_bytes,
                              uint32_t key_bytes, uint32_t digit, void *stream);
 
+/* Same result as raduls_histogram(), without any allocation.  The paper has
+ * no counterpart: this is for callers that cannot let a library allocate
+ * device memory -- an application whose device memory is all reserved up
+ * front by its own allocator, a latency-critical loop that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree, or code running while a
+ * stream is being captured, where allocation calls are not allowed.
+ *
+ * The call's scratch (work counters, the work item, the histogram row and one
+ * u32 per 16384-record tile) lives in a fixed 1 MiB array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Inputs larger than that tile map allows -- more than 260,032 tiles, about
+ * 4.26e9 records -- are rejected with RADULS_ERR_UNSUPPORTED before anything
+ * is launched.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array, and
+ * each call rewrites everything it reads from it, but calls that overlap on
+ * the GPU (for instance on two streams) race on it: serialise them. */
+int raduls_histogram_static(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                            uint32_t digit, uint64_t *d_hist_out, void *stream);
+
 /* Test hook: make the next distribution pass withhold tile `tile`'s published
  * counts so that its successors' bounded waits run out (kind 1), or clear the
  * hook (kind 0).  The pass then reports RADULS_ERR_TIMEOUT through

@@ -9,7 +9,7 @@ built, every call raises.
 from __future__ import annotations
 
 from ._lib import (RaduLSError, RaduLSModel, STATUS, build_library, library_path, load, raduls_debug_inject,
-                   raduls_distribution_pass, raduls_histogram, raduls_set_wait_limit_ns, raduls_sort,
+                   raduls_distribution_pass, raduls_histogram, raduls_histogram_static, raduls_set_wait_limit_ns, raduls_sort,
                    raduls_sort_batched, raduls_sort_ex, raduls_status_string, raduls_stream_status)
 
 __all__ = [
@@ -23,6 +23,7 @@ __all__ = [
     "raduls_sort_ex",
     "raduls_sort_batched",
     "raduls_histogram",
+    "raduls_histogram_static",
     "raduls_distribution_pass",
     "raduls_stream_status",
     "raduls_status_string",

@@ -100,6 +100,7 @@ def load():
             "raduls_sort_ex": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_sort_batched": [vp, vp, vp, u32, u32, u32, vp],
             "raduls_histogram": [vp, u64, u32, u32, u32, vp, vp],
+            "raduls_histogram_static": [vp, u64, u32, u32, u32, vp, vp],
             "raduls_distribution_pass": [vp, vp, u64, u32, u32, u32, vp],
             "raduls_stream_status": [vp],
             "raduls_debug_inject": [u32, u64],
@@ -202,6 +203,16 @@ def raduls_histogram(in_, n_recs: int, rec_bytes: int, key_bytes: int, digit: in
     rc = load().raduls_histogram(_addr(in_), n_recs, rec_bytes, key_bytes, digit, _addr(hist_out),
                                  _stream(stream, in_))
     _raise(rc, "raduls_histogram")
+
+
+def raduls_histogram_static(in_, n_recs: int, rec_bytes: int, key_bytes: int, digit: int, hist_out,
+                            stream=None) -> None:
+    """raduls_histogram() without any allocation (fixed 1 MiB scratch inside the library)."""
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(hist_out, 256 * 8, "hist_out")
+    rc = load().raduls_histogram_static(_addr(in_), n_recs, rec_bytes, key_bytes, digit, _addr(hist_out),
+                                        _stream(stream, in_))
+    _raise(rc, "raduls_histogram_static")
 
 
 def raduls_distribution_pass(in_, out, n_recs: int, rec_bytes: int, key_bytes: int, digit: int,
