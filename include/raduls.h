@@ -71,7 +71,8 @@ enum {
     RADULS_K_BLOCK = 5,     /* on-chip sorts of small-bin runs (Sec. 3.4-3.5) */
     RADULS_K_LEARNED = 6,   /* learned-partition fit, count and distribution */
     RADULS_K_BATCHED = 7,   /* persistent batched segmented sort */
-    RADULS_K_COUNT = 8
+    RADULS_K_BUCKET = 8,    /* mid-size bins: split by one CTA and sorted on chip through L2 (Sec. 3.4) */
+    RADULS_K_COUNT = 9
 };
 
 /* Statistics of one sort, filled when the call returns (the call synchronises
@@ -88,6 +89,8 @@ typedef struct {
     uint32_t learned_fell_back;  /* 1 when the learned partition was rejected */
     float    learned_ratio;      /* max bucket / ideal bucket size of the learned model */
     uint32_t gpu_launches;       /* kernels this call launched */
+    uint64_t bucket_items;       /* mid-size bins split and sorted by one CTA each */
+    uint64_t bucket_bytes;       /* algorithmic bytes read + written by those bins' kernel */
     /* Device time per kernel class, measured with CUDA events recorded on the
      * call's stream around each launch, and launches per class, indexed by
      * the RADULS_K_* classes above. */

@@ -32,6 +32,10 @@ class RaduLSError(RuntimeError):
         super().__init__(f"{where} failed: {STATUS.get(code, code)}")
 
 
+KERNEL_CLASSES = ["setup", "hist", "plan", "scatter", "copy", "block", "learned", "batched", "bucket"]
+N_KERNEL_CLASSES = len(KERNEL_CLASSES)
+
+
 class Stats(ctypes.Structure):
     _fields_ = [
         ("grid_passes", ctypes.c_uint32),
@@ -45,18 +49,19 @@ class Stats(ctypes.Structure):
         ("learned_fell_back", ctypes.c_uint32),
         ("learned_ratio", ctypes.c_float),
         ("gpu_launches", ctypes.c_uint32),
-        ("kernel_ms", ctypes.c_float * 8),
-        ("kernel_launches", ctypes.c_uint32 * 8),
+        ("bucket_items", ctypes.c_uint64),
+        ("bucket_bytes", ctypes.c_uint64),
+        ("kernel_ms", ctypes.c_float * N_KERNEL_CLASSES),
+        ("kernel_launches", ctypes.c_uint32 * N_KERNEL_CLASSES),
     ]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("kernel_ms", "kernel_launches")}
-        d["kernel_ms"] = {KERNEL_CLASSES[i]: float(self.kernel_ms[i]) for i in range(8)}
-        d["kernel_launches"] = {KERNEL_CLASSES[i]: int(self.kernel_launches[i]) for i in range(8)}
+        d["kernel_ms"] = {KERNEL_CLASSES[i]: float(self.kernel_ms[i]) for i in range(N_KERNEL_CLASSES)}
+        d["kernel_launches"] = {KERNEL_CLASSES[i]: int(self.kernel_launches[i]) for i in range(N_KERNEL_CLASSES)}
         return d
 
 
-KERNEL_CLASSES = ["setup", "hist", "plan", "scatter", "copy", "block", "learned", "batched"]
 
 
 class Opts(ctypes.Structure):

@@ -1,424 +1,18 @@
 // blocksort.cu -- on-chip stable sort of small bins (Sec. 3.4-3.5).
 //
-// The paper finishes bins that fit in cache with an unbuffered counting
-// split, and tiny bins (fewer than 384 keys) with comparison sorts (Sec. 3.4,
-// 3.5).  Those comparison sorts (introsort, Shell sort) are not stable; the
-// sort here is defined as stable.  Work items come in two kinds:
+// Work items come in two kinds:
 //   * a RUN: consecutive small sub-bins (at most WARP_MAX records each) of one
-//     parent bin, split on the parent's digit.  The run is loaded into one
-//     CTA's shared memory with coalesced loads, its sub-bin boundaries are
-//     read off a histogram of that digit, and every sub-bin is then sorted by
-//     one warp on its own, without block-wide barriers;
+//     parent bin, split on the parent's digit, or consecutive small arrays of
+//     a batched call.  The run is loaded into one CTA's shared memory with
+//     coalesced loads, its sub-bin boundaries are read off a histogram of that
+//     digit (or the array offsets), and every sub-bin is then sorted by one
+//     warp on its own, without block-wide barriers (warp_sort_bin);
 //   * a single bin of up to CAP records (or a whole small input), sorted by
-//     the whole CTA.
-// Either way the sort mirrors the paper's split between radix passes and
-// comparison sorts for tiny bins: stable counting passes (Sec. 1) on the two
-// most significant key digits that vary inside the bin -- digits on which all
-// its records agree are found from the OR and AND of the key words and
-// skipped -- and then every group of records that still share those digits
-// (tiny for uniform-like keys) is finished by a stable comparison rank: a
-// record's place in its group is the number of members with a smaller key, or
-// an equal key and an earlier position.  A bin with a group larger than
-// TIE_MAX falls back to counting passes over all its varying digits.  Only
-// 16-bit record indices move inside shared memory; the records are read once
-// and written once, in their final order.
-#include "kernels.h"
+//     the whole CTA (block_path).
+// The sorts themselves are in onchip.cuh.
+#include "onchip.cuh"
 
 namespace raduls {
-
-constexpr int MAX_KEY_WORDS = 32;
-constexpr u32 TIE_MAX = 32;                 // largest tie group finished by comparison
-constexpr u32 PRESORT = 2;                  // counting passes before the comparison step
-constexpr u32 WARP_MAX = WARP_BIN;          // sub-bins of a run sorted by one warp
-constexpr int WK = (int)(WARP_MAX / 32);    // elements per lane in the warp sort
-
-template <int THREADS, int K>
-struct BlockSmem {
-    RankSmem<THREADS> rank;
-    unsigned short xidx[THREADS * K];   // exchange buffer: record index at each position
-    unsigned short xcode[THREADS * K];  // presort digits of the record at each position
-    unsigned short xnew[THREADS * K];   // exchange buffer of the comparison step
-    u64 red_or[THREADS / 32];
-    u64 red_and[THREADS / 32];
-    u64 diff[MAX_KEY_WORDS];            // bytes that vary inside the bin, per key word
-    unsigned char vword[8 * MAX_KEY_WORDS];
-    unsigned char vshift[8 * MAX_KEY_WORDS];
-    u32 chist[RADIX];                   // run: records per value of the split digit
-    u32 cpack[RADIX];                   // run: (sub-bin start << 9) | sub-bin slot
-    unsigned short cbeg[RADIX];
-    unsigned short ccnt[RADIX];
-    u32 nchild;
-    u32 nv;                             // number of varying digits
-    u32 item;
-    u32 big_group;
-};
-
-constexpr size_t round16b(size_t x) { return (x + 15) & ~(size_t)15; }
-
-template <int THREADS, int K>
-constexpr size_t block_smem_bytes(u32 rw)
-{
-    return round16b(sizeof(BlockSmem<THREADS, K>)) + ((size_t)THREADS * K * rw + 2) * 8;
-}
-
-// Compare keys of records a and b over words [w0, W) (earlier words are equal
-// inside a bin): -1, 0 or 1.
-__device__ __forceinline__ int key_cmp(const u64 *recs, u32 rw, u32 a, u32 b, u32 w0, u32 kw)
-{
-    for (u32 wi = w0; wi < kw; ++wi) {
-        const u64 x = recs[(u64)a * rw + wi], y = recs[(u64)b * rw + wi];
-        if (x != y)
-            return x < y ? -1 : 1;
-    }
-    return 0;
-}
-
-// ------------------------------------------------------------- block path
-
-// One stable counting pass of the bin on digit (word, shift): the records are
-// re-ranked in their current order and id[] is permuted accordingly.
-template <int THREADS, int K>
-__device__ __forceinline__ void lsd_pass(BlockSmem<THREADS, K> &sm, const u64 *recs, u32 rw, u32 m, u32 kv, u32 word,
-                                         u32 sh, u32 (&id)[K])
-{
-    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
-    u32 dr[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        dr[k] = ((u32)k < kv && pos < m) ? digit_of_word(recs[(u64)id[k] * rw + word], sh) : (u32)(RADIX - 1);
-    }
-    warp_rank<THREADS, K>(sm.rank, dr, kv, m);
-    __syncthreads();
-    u32 total = 0;
-    if (tid < RADIX)
-        total = warp_offsets<THREADS>(sm.rank, tid);
-    scan_totals<THREADS>(sm.rank, total);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        if ((u32)k < kv && pos < m) {
-            const u32 d = dr[k] & 0xffu;
-            sm.xidx[sm.rank.tstart[d] + sm.rank.cnt[w][d] + (dr[k] >> 8)] = (unsigned short)id[k];
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        if ((u32)k < kv && pos < m)
-            id[k] = sm.xidx[pos];
-    }
-    __syncthreads();
-}
-
-// Whole-CTA stable sort of the m records in shared memory by key digits
-// (digit..0); returns the final order in id[] (warp-contiguous positions).
-template <int THREADS, int K>
-__device__ __forceinline__ void block_path(BlockSmem<THREADS, K> &sm, const u64 *recs, u32 rw, u32 m, u32 kv,
-                                           u32 digit, u32 key_words, u32 (&id)[K])
-{
-    constexpr int NW = THREADS / 32;
-    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
-    const u32 top_word = key_words - 1u - digit / 8u;
-    // which key bytes vary inside the bin (words above top_word are shared)
-    for (u32 wi = top_word; wi < key_words && m > 1; ++wi) {
-        u64 vor = 0, vand = ~0ull;
-        for (u32 e = tid; e < m; e += THREADS) {
-            const u64 v = recs[(u64)e * rw + wi];
-            vor |= v;
-            vand &= v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vor |= __shfl_xor_sync(FULL_MASK, vor, o);
-            vand &= __shfl_xor_sync(FULL_MASK, vand, o);
-        }
-        if (lane == 0) {
-            sm.red_or[w] = vor;
-            sm.red_and[w] = vand;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            u64 o2 = 0, a2 = ~0ull;
-#pragma unroll
-            for (int i = 0; i < NW; ++i) {
-                o2 |= sm.red_or[i];
-                a2 &= sm.red_and[i];
-            }
-            u64 diff = o2 ^ a2;
-            if (wi == top_word && (digit % 8u) != 7u)
-                diff &= (2ull << (8u * (digit % 8u) + 7u)) - 1ull;
-            sm.diff[wi] = diff;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        u32 nv = 0;
-        if (m > 1)
-            for (u32 wi = top_word; wi < key_words; ++wi)
-                for (int b = 7; b >= 0; --b)
-                    if ((sm.diff[wi] >> (8 * b)) & 0xffu) {
-                        sm.vword[nv] = (unsigned char)wi;
-                        sm.vshift[nv] = (unsigned char)(8 * b);
-                        ++nv;
-                    }
-        sm.nv = nv;
-    }
-    __syncthreads();
-    const u32 nv = sm.nv;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        id[k] = w * 32u * kv + (u32)k * 32u + lane;
-
-    // 1. counting passes on the top (up to) PRESORT varying digits, least significant first
-    const u32 npre = nv < PRESORT ? nv : PRESORT;
-    for (int v = (int)npre - 1; v >= 0; --v)
-        lsd_pass<THREADS, K>(sm, recs, rw, m, kv, sm.vword[v], sm.vshift[v], id);
-    if (nv <= npre)
-        return;
-    // 2. tie groups: records that share the presorted digits
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        if ((u32)k < kv && pos < m) {
-            u32 c = 0;
-            for (u32 v = 0; v < npre; ++v)
-                c = (c << 8) | digit_of_word(recs[(u64)id[k] * rw + sm.vword[v]], sm.vshift[v]);
-            sm.xcode[pos] = (unsigned short)c;
-        }
-    }
-    __syncthreads();
-    bool tie = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        if ((u32)k < kv && pos + 1 < m)
-            tie |= sm.xcode[pos] == sm.xcode[pos + 1];
-    }
-    if (!__syncthreads_or(tie))
-        return;  // every record's presorted digits differ from its neighbours': the order is final
-    bool big = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-        if ((u32)k < kv && pos < m) {
-            const u32 c = sm.xcode[pos];
-            u32 gl = pos, gr = pos;
-            while (gl > 0 && sm.xcode[gl - 1] == c && pos - gl < TIE_MAX)
-                --gl;
-            while (gr + 1 < m && sm.xcode[gr + 1] == c && gr - pos < TIE_MAX)
-                ++gr;
-            big |= gr - gl + 1 > TIE_MAX;
-        }
-    }
-    if (big)
-        sm.big_group = 1;
-    __syncthreads();
-    if (!sm.big_group) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-            if ((u32)k < kv && pos < m) {
-                const u32 c = sm.xcode[pos];
-                u32 gl = pos, gr = pos;
-                while (gl > 0 && sm.xcode[gl - 1] == c)
-                    --gl;
-                while (gr + 1 < m && sm.xcode[gr + 1] == c)
-                    ++gr;
-                u32 np = gl;
-                for (u32 j = gl; j <= gr; ++j) {
-                    if (j == pos)
-                        continue;
-                    const int cm = key_cmp(recs, rw, sm.xidx[j], id[k], top_word, key_words);
-                    np += (cm < 0 || (cm == 0 && j < pos)) ? 1u : 0u;
-                }
-                sm.xnew[np] = (unsigned short)id[k];
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-            if ((u32)k < kv && pos < m)
-                id[k] = sm.xnew[pos];
-        }
-        __syncthreads();
-    } else {
-        // heavy duplicates: stable LSD over every varying digit from the bin's own order
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-            id[k] = w * 32u * kv + (u32)k * 32u + lane;
-        for (int v = (int)nv - 1; v >= 0; --v)
-            lsd_pass<THREADS, K>(sm, recs, rw, m, kv, sm.vword[v], sm.vshift[v], id);
-    }
-}
-
-// -------------------------------------------------------------- warp path
-
-// Stable counting pass of one sub-bin by one warp: elements e = 32k + lane of
-// the sub-bin [a, a+c) are ranked in order on digit (word, sh) with the warp's
-// own counters, and id[] (chunk-local record indices) is permuted.
-__device__ __forceinline__ void warp_lsd_pass(u32 *cnt, unsigned short *xidx, const u64 *recs, u32 rw, u32 a, u32 c,
-                                              u32 word, u32 sh, u32 (&id)[WK])
-{
-    const u32 lane = threadIdx.x & 31u;
-    const u32 lt = lanemask_lt();
-    for (u32 i = lane; i < RADIX; i += 32)
-        cnt[i] = 0;
-    __syncwarp();
-    u32 dr[WK];
-#pragma unroll
-    for (int k = 0; k < WK; ++k) {
-        if ((u32)k * 32u < c) {
-            const u32 e = (u32)k * 32u + lane;
-            const u32 d = e < c ? digit_of_word(recs[(u64)id[k] * rw + word], sh) : (u32)(RADIX - 1);
-            const u32 peers = peers_of<8>(d);
-            const u32 prev = cnt[d];
-            __syncwarp();
-            if ((peers & lt) == 0)
-                cnt[d] = prev + __popc(peers);
-            __syncwarp();
-            dr[k] = d | ((prev + __popc(peers & lt)) << 8);
-        }
-    }
-    // exclusive scan of the 256 counters: lane l owns digits 8l .. 8l+7
-    u32 v[8], s = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v[i] = cnt[8 * lane + i];
-        s += v[i];
-    }
-    u32 incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u32 t = __shfl_up_sync(FULL_MASK, incl, o);
-        if (lane >= (u32)o)
-            incl += t;
-    }
-    u32 run = incl - s;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        cnt[8 * lane + i] = run;
-        run += v[i];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < WK; ++k) {
-        const u32 e = (u32)k * 32u + lane;
-        if ((u32)k * 32u < c && e < c)
-            xidx[a + cnt[dr[k] & 0xffu] + (dr[k] >> 8)] = (unsigned short)id[k];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < WK; ++k) {
-        const u32 e = (u32)k * 32u + lane;
-        if ((u32)k * 32u < c && e < c)
-            id[k] = xidx[a + e];
-    }
-    __syncwarp();
-}
-
-// Sort sub-bin [a, a+c) of the run in shared memory and write it to out.  One
-// warp; c <= WARP_MAX.  vword/vshift list the run's varying digits below its
-// split digit, most significant first (a superset of the sub-bin's own).
-template <int RW>
-__device__ void warp_sort_bin(u32 *cnt, unsigned short *xidx, unsigned short *xcode, unsigned short *xnew,
-                              const u64 *recs, u32 rw, u32 a, u32 c, const unsigned char *vword,
-                              const unsigned char *vshift, u32 nv, u32 w0, u32 key_words, u64 *out)
-{
-    const u32 lane = threadIdx.x & 31u;
-    u32 id[WK];
-#pragma unroll
-    for (int k = 0; k < WK; ++k)
-        id[k] = a + (u32)k * 32u + lane;
-    if (c > 1) {
-        const u32 npre = nv < PRESORT ? nv : PRESORT;
-        for (int v = (int)npre - 1; v >= 0; --v)
-            warp_lsd_pass(cnt, xidx, recs, rw, a, c, vword[v], vshift[v], id);
-        if (nv > npre) {
-            // records whose presorted digits equal a neighbour's may still be out of order
-#pragma unroll
-            for (int k = 0; k < WK; ++k) {
-                const u32 e = (u32)k * 32u + lane;
-                if ((u32)k * 32u < c && e < c) {
-                    u32 cd = 0;
-                    for (u32 v = 0; v < npre; ++v)
-                        cd = (cd << 8) | digit_of_word(recs[(u64)id[k] * rw + vword[v]], vshift[v]);
-                    xcode[a + e] = (unsigned short)cd;
-                }
-            }
-            __syncwarp();
-            bool tie = false;
-#pragma unroll
-            for (int k = 0; k < WK; ++k) {
-                const u32 e = (u32)k * 32u + lane;
-                if ((u32)k * 32u < c && e + 1 < c)
-                    tie |= xcode[a + e] == xcode[a + e + 1];
-            }
-            if (__any_sync(FULL_MASK, tie)) {
-                bool big = false;
-#pragma unroll
-                for (int k = 0; k < WK; ++k) {
-                    const u32 e = (u32)k * 32u + lane;
-                    if ((u32)k * 32u < c && e < c) {
-                        const u32 cd = xcode[a + e];
-                        u32 gl = e, gr = e;
-                        while (gl > 0 && xcode[a + gl - 1] == cd && e - gl < TIE_MAX)
-                            --gl;
-                        while (gr + 1 < c && xcode[a + gr + 1] == cd && gr - e < TIE_MAX)
-                            ++gr;
-                        big |= gr - gl + 1 > TIE_MAX;
-                    }
-                }
-                if (!__any_sync(FULL_MASK, big)) {
-                    // stable comparison rank inside each tie group
-#pragma unroll
-                    for (int k = 0; k < WK; ++k) {
-                        const u32 e = (u32)k * 32u + lane;
-                        if ((u32)k * 32u < c && e < c) {
-                            const u32 cd = xcode[a + e];
-                            u32 gl = e, gr = e;
-                            while (gl > 0 && xcode[a + gl - 1] == cd)
-                                --gl;
-                            while (gr + 1 < c && xcode[a + gr + 1] == cd)
-                                ++gr;
-                            u32 np = gl;
-                            for (u32 j = gl; j <= gr; ++j) {
-                                if (j == e)
-                                    continue;
-                                const int cm = key_cmp(recs, rw, xidx[a + j], id[k], w0, key_words);
-                                np += (cm < 0 || (cm == 0 && j < e)) ? 1u : 0u;
-                            }
-                            xnew[a + np] = (unsigned short)id[k];
-                        }
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int k = 0; k < WK; ++k) {
-                        const u32 e = (u32)k * 32u + lane;
-                        if ((u32)k * 32u < c && e < c)
-                            id[k] = xnew[a + e];
-                    }
-                    __syncwarp();
-                } else {
-                    // heavy duplicates: LSD over every varying digit, from the sub-bin's own order
-#pragma unroll
-                    for (int k = 0; k < WK; ++k)
-                        id[k] = a + (u32)k * 32u + lane;
-                    for (int v = (int)nv - 1; v >= 0; --v)
-                        warp_lsd_pass(cnt, xidx, recs, rw, a, c, vword[v], vshift[v], id);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < WK; ++k) {
-        const u32 e = (u32)k * 32u + lane;
-        if ((u32)k * 32u < c && e < c)
-            copy_record<RW>(out + (u64)(a + e) * rw, recs + (u64)id[k] * rw, rw);
-    }
-}
 
 // ------------------------------------------------------------------ kernel
 
@@ -484,49 +78,8 @@ block_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
                     }
                 }
             }
-            // key digits below p that vary anywhere in the run (OR / AND of each key word)
-            for (u32 wi = p_word; wi < key_words; ++wi) {
-                u64 vor = 0, vand = ~0ull;
-                for (u32 e = tid; e < m; e += THREADS) {
-                    const u64 x = recs[(u64)e * rw + wi];
-                    vor |= x;
-                    vand &= x;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    vor |= __shfl_xor_sync(FULL_MASK, vor, o);
-                    vand &= __shfl_xor_sync(FULL_MASK, vand, o);
-                }
-                if (lane == 0) {
-                    sm.red_or[w] = vor;
-                    sm.red_and[w] = vand;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    u64 o2 = 0, a2 = ~0ull;
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) {
-                        o2 |= sm.red_or[i];
-                        a2 &= sm.red_and[i];
-                    }
-                    u64 diff = o2 ^ a2;
-                    if (wi == p_word && p_byte < 8u)
-                        diff &= (p_byte == 0) ? 0ull : ((1ull << (8u * p_byte)) - 1ull);
-                    sm.diff[wi] = diff;
-                }
-                __syncthreads();
-            }
-            if (tid == 0) {
-                u32 nv = 0;
-                for (u32 wi = p_word; wi < key_words; ++wi)
-                    for (int b2 = 7; b2 >= 0; --b2)
-                        if ((sm.diff[wi] >> (8 * b2)) & 0xffu) {
-                            sm.vword[nv] = (unsigned char)wi;
-                            sm.vshift[nv] = (unsigned char)(8 * b2);
-                            ++nv;
-                        }
-                sm.nv = nv;
-            }
+            // key digits below p that vary anywhere in the run
+            varying_digits_below<THREADS, K>(sm, recs, rw, m, p_word, p_byte, key_words);
             if (segs) {
                 // arrays [tile_base, tile_base + row) of the offset table (row <= 256)
                 const u64 o0 = seg_off[item.tile_base];

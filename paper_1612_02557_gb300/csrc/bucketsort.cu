@@ -1,0 +1,766 @@
+// bucketsort.cu -- mid-size bins: one CTA sorts a whole bin through L2.
+//
+// A bin too big for one CTA's shared memory but small enough to stay in L2
+// (up to 40,960 records) would cost a full device-wide level if it went the
+// way of the big bins (Sec. 3.3): a histogram pass, a distribution pass, and
+// then on-chip sorts that read the sub-bins back from HBM.  The paper keeps
+// such bins in cache and splits them there (Sec. 3.4).  Here one CTA takes the
+// whole bin and reads it from HBM once:
+//   1. histogram of the 16-bit code formed by the bin's two most significant
+//      varying digits (65,536 counters of 16 bits in shared memory), together
+//      with the OR and AND of the key words, which find those digits;
+//   2. exclusive prefix of the counters: the start of every code's group;
+//   3. placement: every record goes to the next free slot of its code's group
+//      in the other buffer (a shared-memory atomic), while its original index
+//      in the bin is kept in shared memory.  The slots taken inside a group
+//      need not follow the input order;
+//   4. groups are tiny (the bin holds fewer records than there are codes), so
+//      each group's final order is settled by ranking its members by (key,
+//      original index) -- exactly the stable order -- and the records are
+//      written to their final place in `in`.  The scratch copy is then dropped
+//      from L2 without being written back.
+// A bin whose largest code group exceeds GROUP_MAX (heavy duplicates, or few
+// varying bits) is instead split stably on its top varying digit, chunk by
+// chunk (the counting split of Sec. 1, with running offsets in shared memory),
+// and its sub-bins are sorted on chip group by group (onchip.cuh); sub-bins
+// too big for shared memory go on to the next level.
+#include "onchip.cuh"
+
+namespace raduls {
+
+constexpr u32 CODE_WORDS = 32768;  // 65,536 16-bit counters, two per word
+constexpr u32 GROUP_MAX = 16;      // largest code group settled by ranking
+
+// Shared memory of the stable split (fallback path).
+template <int THREADS, int K, int KS>
+struct BucketSplitSmem {
+    BlockSmem<THREADS, K> b;           // on-chip sort scratch; b.xnew holds the split's permutation
+    u32 run[RADIX];                    // next slot of every sub-bin (relative to the bin)
+    u32 goff[RADIX];                   // run[d] - tstart[d] for the current chunk
+    u32 cbeg[RADIX + 1];               // sub-bin starts relative to the bin (cbeg[256] = count)
+    unsigned short glist[RADIX + 1];   // first sub-bin of every group
+    u32 gsum[RADIX / 32];
+    u32 ngroups;
+};
+
+// Shared memory of the code-group path.
+struct BucketCodeSmem {
+    u32 cnt[CODE_WORDS];                   // 16-bit counters -> group starts -> group ends
+    unsigned short oidx[BUCKET_IDX_MAX];   // original index of the record at each placed slot
+};
+
+template <int THREADS>
+struct BucketCommon {
+    static constexpr int NW = THREADS / 32;
+    u64 red_or[2][NW];
+    u64 red_and[2][NW];
+    u64 diff[MAX_KEY_WORDS];
+    u32 hist8[RADIX];   // records per value of the top varying digit
+    u32 wsum[NW];
+    u32 wmax[NW];
+    u32 item;
+    u32 maxc;
+    int t1, t2;         // the code's digits (t2 < 0: one varying digit only)
+};
+
+template <int THREADS, int K, int KS>
+constexpr size_t bucket_buf_words(u32 rw)
+{
+    // two split chunks (each with its 16-byte phase word) or one on-chip group
+    const size_t chunks = 2 * ((size_t)THREADS * KS * rw + 2);
+    const size_t group = (size_t)THREADS * K * rw + 2;
+    return (chunks > group ? chunks : group) + 2;
+}
+
+// Drop the L2 lines that lie wholly inside bytes [lo, hi) of global memory.
+template <int THREADS>
+__device__ __forceinline__ void discard_range(const void *lo, const void *hi)
+{
+    const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
+    for (uintptr_t x = a + (uintptr_t)threadIdx.x * 128; x < b; x += (uintptr_t)THREADS * 128)
+        discard_l2_line((const void *)x);
+}
+
+// Word w of a record held in registers (unrolled select: no local memory).
+template <int RW>
+__device__ __forceinline__ u64 rec_word(const u64 (&r)[RW], u32 w)
+{
+    u64 x = r[0];
+#pragma unroll
+    for (int i = 1; i < RW; ++i)
+        if (w == (u32)i)
+            x = r[i];
+    return x;
+}
+
+template <int RW>
+__device__ __forceinline__ void load_rec(u64 (&r)[RW], const u64 *g)
+{
+    if constexpr (RW == 1) {
+        r[0] = __ldcg(g);
+    } else {
+#pragma unroll
+        for (int i = 0; i < RW; i += 2) {
+            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(g + i));
+            r[i] = v.x;
+            r[i + 1] = v.y;
+        }
+    }
+}
+
+template <int RW>
+__device__ __forceinline__ void store_rec(u64 *g, const u64 (&r)[RW])
+{
+    if constexpr (RW == 1) {
+        g[0] = r[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < RW; i += 2)
+            *reinterpret_cast<ulonglong2 *>(g + i) = make_ulonglong2(r[i], r[i + 1]);
+    }
+}
+
+// Location of digit t: word and shift.
+struct DigitLoc {
+    u32 word, sh;
+};
+
+__device__ __forceinline__ DigitLoc digit_loc(u32 t, u32 key_words)
+{
+    return DigitLoc{key_words - 1u - t / 8u, 8u * (t % 8u)};
+}
+
+// 16-bit code of a record from its key words.
+__device__ __forceinline__ u32 code_of(u64 wa, u64 wb, const DigitLoc &la, const DigitLoc &lb, bool two)
+{
+    const u32 hi = (u32)(wa >> la.sh) & 0xffu;
+    const u32 lo = two ? (u32)(wb >> lb.sh) & 0xffu : 0u;
+    return (hi << 8) | lo;
+}
+
+__device__ __forceinline__ u32 get16(const u32 *cnt, u32 code)
+{
+    return (cnt[code >> 1] >> ((code & 1u) << 4)) & 0xffffu;
+}
+
+// Key order of two records of a bin (words below `w0` are equal): then the
+// original index decides.
+__device__ __forceinline__ bool rec_less(const u64 *x, const u64 *y, u32 ox, u32 oy, u32 w0, u32 key_words)
+{
+    for (u32 w = w0; w < key_words; ++w) {
+        const u64 a = __ldcg(x + w), b = __ldcg(y + w);
+        if (a != b)
+            return a < b;
+    }
+    return ox < oy;
+}
+
+template <int THREADS, int RW>
+__global__ void __launch_bounds__(THREADS, 1)
+bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
+{
+    using Common = BucketCommon<THREADS>;
+    constexpr int NW = THREADS / 32;
+    constexpr u32 CW = CODE_WORDS / THREADS;  // counter words per thread
+    static_assert(CODE_WORDS % THREADS == 0 && RADIX * 256 / (2 * CW) == THREADS,
+                  "four threads per value of the top digit");
+    static_assert(RW >= 1, "compile-time record width");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Common &cm = *reinterpret_cast<Common *>(smem_raw);
+    BucketCodeSmem &cs = *reinterpret_cast<BucketCodeSmem *>(smem_raw + round16b(sizeof(Common)));
+    const u32 rw = (u32)RW;
+    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    const u32 key_words = a.key_words;
+    const u32 n_items = a.ctrs->bucket_cur;
+
+    for (;;) {
+        if (tid == 0)
+            cm.item = atomicAdd(&a.ctrs->tile_ctr[4], 1u);
+        __syncthreads();
+        const u32 ii = cm.item;
+        if (ii >= n_items)
+            break;
+        const WorkItem item = a.buckets_cur[ii];
+        if (item.count > a.bucket_max || item.count > BUCKET_IDX_MAX || item.count < 2 ||
+            item.digit >= 8u * key_words) {  // planner guard
+            if (tid == 0)
+                set_error(a.ctrs, ST_INTERNAL);
+            __syncthreads();
+            continue;
+        }
+        const u32 n = (u32)item.count;
+        const u32 p = item.digit;
+        const bool from_tmp = (item.flags & ITEM_IN_TMP) != 0;
+        const u64 *src = (from_tmp ? tmp : in) + item.begin * rw;
+        u64 *stg = (from_tmp ? in : tmp) + item.begin * rw;  // the bin's range of the other buffer
+        u64 *out = in + item.begin * rw;
+        if (tid == 0) {
+            atomicAdd(&a.ctrs->bucket_bytes, 2ull * n * rw * 8u);
+            atomicAdd(&a.ctrs->bucket_items, 1ull);
+        }
+
+        // ---- 1. histogram of the code of digits (p, p-1), OR / AND of their words
+        for (u32 i = tid; i < CODE_WORDS; i += THREADS)
+            cs.cnt[i] = 0;
+        __syncthreads();
+        DigitLoc la = digit_loc(p, key_words), lb = digit_loc(p > 0 ? p - 1u : 0u, key_words);
+        bool two = p > 0;
+        {
+            // U1 key words in flight per thread before their counters are bumped
+            constexpr u32 U1 = 4;
+            const bool same = la.word == lb.word;
+            u64 o0 = 0, a0 = ~0ull, o1 = 0, a1 = ~0ull;
+            for (u32 i0 = tid; i0 < n; i0 += THREADS * U1) {
+                u64 wa[U1], wb[U1];
+#pragma unroll
+                for (u32 k = 0; k < U1; ++k) {
+                    const u32 i = i0 + k * THREADS;
+                    wa[k] = i < n ? __ldcg(src + (u64)i * rw + la.word) : 0ull;
+                    wb[k] = (i < n && !same) ? __ldcg(src + (u64)i * rw + lb.word) : wa[k];
+                }
+#pragma unroll
+                for (u32 k = 0; k < U1; ++k) {
+                    if (i0 + k * THREADS < n) {
+                        o0 |= wa[k];
+                        a0 &= wa[k];
+                        o1 |= wb[k];
+                        a1 &= wb[k];
+                        const u32 c = code_of(wa[k], wb[k], la, lb, two);
+                        atomicAdd(&cs.cnt[c >> 1], 1u << ((c & 1u) << 4));
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                o0 |= __shfl_xor_sync(FULL_MASK, o0, o);
+                a0 &= __shfl_xor_sync(FULL_MASK, a0, o);
+                o1 |= __shfl_xor_sync(FULL_MASK, o1, o);
+                a1 &= __shfl_xor_sync(FULL_MASK, a1, o);
+            }
+            if (lane == 0) {
+                cm.red_or[0][w] = o0;
+                cm.red_and[0][w] = a0;
+                cm.red_or[1][w] = o1;
+                cm.red_and[1][w] = a1;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            u64 o0 = 0, a0 = ~0ull, o1 = 0, a1 = ~0ull;
+            for (int i = 0; i < NW; ++i) {
+                o0 |= cm.red_or[0][i];
+                a0 &= cm.red_and[0][i];
+                o1 |= cm.red_or[1][i];
+                a1 &= cm.red_and[1][i];
+            }
+            const bool vp = (((o0 ^ a0) >> la.sh) & 0xffu) != 0;
+            const bool vq = two && (((o1 ^ a1) >> lb.sh) & 0xffu) != 0;
+            cm.t1 = (vp && vq) ? (int)p : -2;  // -2: the speculation missed
+            cm.t2 = (vp && vq) ? (int)p - 1 : -2;
+        }
+        __syncthreads();
+        if (cm.t1 == -2) {
+            // some of digits p, p-1 are constant here: find the bin's two most
+            // significant varying digits from the OR / AND of every key word
+            for (u32 wi = la.word; wi < key_words; ++wi) {
+                u64 vo = 0, va = ~0ull;
+                for (u32 i = tid; i < n; i += THREADS) {
+                    const u64 x = __ldcg(src + (u64)i * rw + wi);
+                    vo |= x;
+                    va &= x;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vo |= __shfl_xor_sync(FULL_MASK, vo, o);
+                    va &= __shfl_xor_sync(FULL_MASK, va, o);
+                }
+                if (lane == 0) {
+                    cm.red_or[0][w] = vo;
+                    cm.red_and[0][w] = va;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    u64 o2 = 0, a2 = ~0ull;
+                    for (int i = 0; i < NW; ++i) {
+                        o2 |= cm.red_or[0][i];
+                        a2 &= cm.red_and[0][i];
+                    }
+                    u64 d = o2 ^ a2;
+                    if (wi == la.word && p % 8u != 7u)
+                        d &= (2ull << (8u * (p % 8u) + 7u)) - 1ull;  // bytes at or below digit p
+                    cm.diff[wi] = d;
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                int t1 = -1, t2 = -1;
+                for (int t = (int)p; t >= 0 && t2 < 0; --t) {
+                    const DigitLoc l = digit_loc((u32)t, key_words);
+                    if ((cm.diff[l.word] >> l.sh) & 0xffu) {
+                        if (t1 < 0)
+                            t1 = t;
+                        else
+                            t2 = t;
+                    }
+                }
+                cm.t1 = t1;
+                cm.t2 = t2;
+            }
+            __syncthreads();
+            if (cm.t1 < 0) {
+                // every key of the bin is equal: its order is final
+                if (from_tmp) {
+                    for (u64 i = tid; i < (u64)n * rw; i += THREADS)
+                        out[i] = __ldcg(src + i);
+                }
+                __syncthreads();
+                continue;
+            }
+            la = digit_loc((u32)cm.t1, key_words);
+            two = cm.t2 >= 0;
+            lb = digit_loc(two ? (u32)cm.t2 : 0u, key_words);
+            for (u32 i = tid; i < CODE_WORDS; i += THREADS)
+                cs.cnt[i] = 0;
+            __syncthreads();
+            for (u32 i = tid; i < n; i += THREADS) {
+                const u64 wa = __ldcg(src + (u64)i * rw + la.word);
+                const u64 wb = __ldcg(src + (u64)i * rw + lb.word);
+                const u32 c = code_of(wa, wb, la, lb, two);
+                atomicAdd(&cs.cnt[c >> 1], 1u << ((c & 1u) << 4));
+            }
+            __syncthreads();
+        }
+        const u32 t1 = (u32)cm.t1;
+
+        // ---- 2. group sizes: sums, largest group, the top digit's histogram
+        u32 sum = 0, mx = 0;
+        for (u32 j = 0; j < CW; ++j) {
+            const u32 v = cs.cnt[tid * CW + j];
+            const u32 lo = v & 0xffffu, hi = v >> 16;
+            sum += lo + hi;
+            mx = max(mx, max(lo, hi));
+        }
+        {
+            // four consecutive threads cover the 256 codes of one top-digit value
+            u32 s4 = sum + __shfl_down_sync(FULL_MASK, sum, 1);
+            s4 += __shfl_down_sync(FULL_MASK, s4, 2);
+            if ((tid & 3u) == 0)
+                cm.hist8[tid >> 2] = s4;
+            u32 incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 v = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= (u32)o)
+                    incl += v;
+            }
+            u32 wm = mx;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                wm = max(wm, __shfl_xor_sync(FULL_MASK, wm, o));
+            if (lane == 31)
+                cm.wsum[w] = incl;
+            if (lane == 0)
+                cm.wmax[w] = wm;
+            __syncthreads();
+            u32 before = 0, m2 = 0;
+            for (int i = 0; i < NW; ++i) {
+                before += (i < (int)w) ? cm.wsum[i] : 0u;
+                m2 = max(m2, cm.wmax[i]);
+            }
+            sum = before + incl - sum;  // exclusive start of this thread's codes
+            mx = m2;
+        }
+
+        if (mx <= GROUP_MAX) {
+            // this CTA's private scratch region (reused bin after bin, so it stays in L2)
+            u64 *const scr = a.bucket_scratch + (u64)blockIdx.x * a.bucket_max * rw;
+            // ---- 3. placement by code (group starts -> running ends), original index kept
+            u32 run = sum;
+            for (u32 j = 0; j < CW; ++j) {
+                const u32 v = cs.cnt[tid * CW + j];
+                const u32 lo = v & 0xffffu, hi = v >> 16;
+                cs.cnt[tid * CW + j] = run | ((run + lo) << 16);
+                run += lo + hi;
+            }
+            __syncthreads();
+            constexpr u32 U = RW >= 4 ? 2u : 4u;  // records in flight per thread
+            for (u32 i0 = tid; i0 < n; i0 += THREADS * U) {
+                u64 r[U][RW];
+#pragma unroll
+                for (u32 k = 0; k < U; ++k) {
+                    const u32 i = i0 + k * THREADS;
+                    if (i < n)
+                        load_rec<RW>(r[k], src + (u64)i * rw);
+                }
+#pragma unroll
+                for (u32 k = 0; k < U; ++k) {
+                    const u32 i = i0 + k * THREADS;
+                    if (i < n) {
+                        const u32 c = code_of(rec_word<RW>(r[k], la.word), rec_word<RW>(r[k], lb.word), la, lb, two);
+                        const u32 sh = (c & 1u) << 4;
+                        const u32 pos = (atomicAdd(&cs.cnt[c >> 1], 1u << sh) >> sh) & 0xffffu;
+                        if (pos < n) {
+                            store_rec<RW>(scr + (u64)pos * rw, r[k]);
+                            cs.oidx[pos] = (unsigned short)i;
+                        } else {
+                            set_error(a.ctrs, ST_INTERNAL);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- 4. final places: slot q of code group [s, e) goes to s + its rank
+            // in the group by (key, original index).  Consecutive slots sit in
+            // consecutive lanes, so a group inside the warp's window of 32 slots
+            // is ranked with shuffles; one that straddles windows reads the
+            // other members' keys back from the scratch copy.
+            const u32 w0 = digit_loc(t1, key_words).word;  // earlier key words are equal in the bin
+            constexpr u32 U4 = RW >= 4 ? 2u : 4u;
+            for (u32 b0 = 0; b0 < n; b0 += THREADS * U4) {  // same trip count in every lane (shuffles)
+                const u32 q0 = b0 + tid;
+                u64 rr[U4][RW];
+#pragma unroll
+                for (u32 k = 0; k < U4; ++k)
+                    if (q0 + k * THREADS < n)
+                        load_rec<RW>(rr[k], scr + (u64)(q0 + k * THREADS) * rw);
+#pragma unroll
+                for (u32 k = 0; k < U4; ++k) {
+                    const u32 q = q0 + k * THREADS;
+                    const bool valid = q < n;
+                    u32 s = q, g = 1, oq = 0;
+                    u64 kq = 0;
+                    if (valid) {
+                        const u32 c = code_of(rec_word<RW>(rr[k], la.word), rec_word<RW>(rr[k], lb.word), la, lb,
+                                              two);
+                        const u32 e = get16(cs.cnt, c);
+                        s = c ? get16(cs.cnt, c - 1u) : 0u;
+                        g = e - s;
+                        oq = cs.oidx[q];
+                        kq = rec_word<RW>(rr[k], w0);
+                    }
+                    const u32 wb = q - lane;  // first slot of this warp's window
+                    const bool inwin = valid && g > 1 && s >= wb && s + g <= wb + 32u;
+                    u32 rank = 0;
+                    const u32 gmax = __reduce_max_sync(FULL_MASK, inwin ? g : 0u);
+                    for (u32 j = 0; j < gmax; ++j) {
+                        const u32 sl = (inwin && j < g) ? s - wb + j : lane;
+                        const u64 kx = __shfl_sync(FULL_MASK, kq, sl);
+                        const u32 ox = __shfl_sync(FULL_MASK, oq, sl);
+                        if (inwin && j < g && s + j != q) {
+                            bool lt;
+                            if (kx != kq)
+                                lt = kx < kq;
+                            else if (w0 + 1 < key_words)
+                                lt = rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, ox, oq, w0 + 1, key_words);
+                            else
+                                lt = ox < oq;
+                            rank += lt ? 1u : 0u;
+                        }
+                    }
+                    if (valid && g > 1 && !inwin) {
+                        for (u32 j = 0; j < g; ++j)
+                            if (s + j != q && rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, cs.oidx[s + j], oq,
+                                                       w0, key_words))
+                                ++rank;
+                    }
+                    if (valid)
+                        store_rec<RW>(out + (u64)(g > 1 ? s + rank : q) * rw, rr[k]);
+                }
+            }
+            __syncthreads();
+            // the scratch copy is dead: drop it from L2 unwritten
+            discard_range<THREADS>(scr, scr + (u64)n * rw);
+            __syncthreads();
+            continue;
+        }
+
+        // heavy code groups: the stable split below (bucket_split_kernel) takes the bin,
+        // starting at its top varying digit
+        if (tid == 0) {
+            const u32 slot = atomicAdd(&a.ctrs->bucket_split, 1u);
+            if (slot < a.caps.grid) {
+                WorkItem it = item;
+                it.digit = t1;
+                a.buckets_split[slot] = it;
+            } else {
+                set_error(a.ctrs, ST_INTERNAL);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Stable split of a mid-size bin on digit item.digit (its top varying digit),
+// chunk by chunk into the other buffer, then on-chip sorts of its sub-bins,
+// group by group; sub-bins bigger than one group go on to the next level.
+template <int THREADS, int K, int KS, int RW>
+__global__ void __launch_bounds__(THREADS, 1)
+bucket_split_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
+{
+    using SplitSm = BucketSplitSmem<THREADS, K, KS>;
+    constexpr u32 CAP = THREADS * K, T = THREADS * KS;
+    constexpr int NW = THREADS / 32;
+    static_assert(T <= CAP && CAP <= 65536, "16-bit record indices");
+    static_assert(CAP > WARP_MAX, "a group holds at least one warp-sized sub-bin");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SplitSm &sm = *reinterpret_cast<SplitSm *>(smem_raw);
+    u64 *const buf0 = reinterpret_cast<u64 *>(smem_raw + round16b(sizeof(SplitSm)));
+    const u32 rw = (u32)RW;
+    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    const u32 key_words = a.key_words;
+    const u32 n_items = a.ctrs->bucket_split;
+
+    for (;;) {
+        if (tid == 0)
+            sm.b.item = atomicAdd(&a.ctrs->split_ctr, 1u);
+        __syncthreads();
+        const u32 ii = sm.b.item;
+        if (ii >= n_items)
+            break;
+        const WorkItem item = a.buckets_split[ii];
+        if (item.count > BUCKET_IDX_MAX || item.count < 2 || item.digit >= 8u * key_words) {  // guard
+            if (tid == 0)
+                set_error(a.ctrs, ST_INTERNAL);
+            __syncthreads();
+            continue;
+        }
+        const u32 n = (u32)item.count;
+        const u32 t1 = item.digit;
+        const bool from_tmp = (item.flags & ITEM_IN_TMP) != 0;
+        const u64 *src = (from_tmp ? tmp : in) + item.begin * rw;
+        u64 *stg = (from_tmp ? in : tmp) + item.begin * rw;
+        u64 *out = in + item.begin * rw;
+        const u32 p_word = digit_loc(t1, key_words).word, p_sh = digit_loc(t1, key_words).sh;
+        // histogram of digit t1 (per-warp counters, summed per digit)
+        for (u32 i = lane; i < RADIX + 1; i += 32)
+            sm.b.rank.cnt[w][i] = 0;
+        __syncthreads();
+        for (u32 i = tid; i < n; i += THREADS)
+            atomicAdd(&sm.b.rank.cnt[w][digit_of_word(__ldcg(src + (u64)i * rw + p_word), p_sh)], 1u);
+        __syncthreads();
+        if (tid < RADIX) {
+            u32 h = 0;
+            for (int i = 0; i < NW; ++i)
+                h += sm.b.rank.cnt[i][tid];
+            u32 incl = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 v = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= (u32)o)
+                    incl += v;
+            }
+            if (lane == 31)
+                sm.gsum[w] = incl;
+            bar_sync_named(1, RADIX);
+            u32 before = 0;
+            for (u32 i = 0; i < w; ++i)
+                before += sm.gsum[i];
+            const u32 c0 = before + incl - h;
+            sm.run[tid] = c0;
+            sm.cbeg[tid] = c0;
+        }
+        if (tid == 0)
+            sm.cbeg[RADIX] = n;
+        unsigned short *const perm = sm.b.xnew;
+        const u32 nchunks = (n + T - 1) / T;
+        auto chunk_buf = [&](u32 c) {
+            const u64 g0 = (item.begin + (u64)c * T) * rw;
+            return buf0 + (size_t)(c & 1u) * ((size_t)T * rw + 2) + (g0 & 1u);
+        };
+        auto chunk_len = [&](u32 c) { return n - c * T < T ? n - c * T : T; };
+        __syncthreads();
+        load_words_async<THREADS>(chunk_buf(0), src, (u64)chunk_len(0) * rw);
+        cp_async_commit();
+        for (u32 c = 0; c < nchunks; ++c) {
+            if (c + 1 < nchunks)
+                load_words_async<THREADS>(chunk_buf(c + 1), src + (u64)(c + 1) * T * rw, (u64)chunk_len(c + 1) * rw);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+            const u32 m = chunk_len(c);
+            const u64 *recs = chunk_buf(c);
+            u32 dr[KS];
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+                const u32 e = w * 32u * KS + (u32)k * 32u + lane;
+                dr[k] = e < m ? digit_of_word(recs[(u64)e * rw + p_word], p_sh) : (u32)(RADIX - 1);
+            }
+            warp_rank<THREADS, KS>(sm.b.rank, dr);
+            __syncthreads();
+            u32 total = 0;
+            if (tid < RADIX) {
+                total = warp_offsets<THREADS>(sm.b.rank, tid);
+                if (tid == RADIX - 1)
+                    total -= T - m;  // padding elements of a partial chunk
+            }
+            scan_totals<THREADS>(sm.b.rank, total);
+            if (tid < RADIX) {
+                sm.goff[tid] = sm.run[tid] - sm.b.rank.tstart[tid];
+                sm.run[tid] += total;
+            }
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+                const u32 e = w * 32u * KS + (u32)k * 32u + lane;
+                if (e < m) {
+                    const u32 d = dr[k] & 0xffu;
+                    perm[sm.b.rank.tstart[d] + sm.b.rank.cnt[w][d] + (dr[k] >> 8)] = (unsigned short)e;
+                }
+            }
+            __syncthreads();
+            // slot s of the chunk's digit-sorted order goes to goff[d] + s: each
+            // digit's records leave as one contiguous run
+            for (u32 s = tid; s < m; s += THREADS) {
+                const u64 *r = recs + (u64)perm[s] * rw;
+                const u32 d = digit_of_word(r[p_word], p_sh);
+                const u32 pos = sm.goff[d] + s;  // u32 arithmetic: goff may wrap below zero
+                if (pos < n)
+                    copy_record<RW>(stg + (u64)pos * rw, r, rw);
+                else
+                    set_error(a.ctrs, ST_INTERNAL);  // histogram and data disagree: never write outside the bin
+            }
+            __syncthreads();
+        }
+        if (t1 == 0) {
+            // no digit left: every sub-bin holds one key, already in input order
+            if (!from_tmp) {
+                for (u64 i = tid; i < (u64)n * rw; i += THREADS)
+                    out[i] = __ldcg(stg + i);
+                __syncthreads();
+                discard_range<THREADS>(stg, stg + (u64)n * rw);
+            }
+            __syncthreads();
+            continue;
+        }
+        const u32 stg_flag = from_tmp ? 0u : ITEM_IN_TMP;
+        if (tid < RADIX) {
+            // group heads: a sub-bin too big for a warp starts (and is) a group of
+            // its own; consecutive small sub-bins share a group while their starts
+            // fall in the same window of CAP - WARP_MAX records (so a group holds
+            // at most CAP records)
+            const u32 gw = CAP - WARP_MAX;
+            const u32 cnt = sm.cbeg[tid + 1] - sm.cbeg[tid];
+            const bool small = cnt <= WARP_MAX;
+            bool head = true;
+            if (tid > 0 && small) {
+                const u32 pc = sm.cbeg[tid] - sm.cbeg[tid - 1];
+                head = pc > WARP_MAX || sm.cbeg[tid - 1] / gw != sm.cbeg[tid] / gw;
+            }
+            if (cnt > CAP)  // stays in the other buffer for the next level
+                append_bin(a, item.begin + sm.cbeg[tid], cnt, t1 - 1u, stg_flag);
+            const u32 bal = __ballot_sync(FULL_MASK, head);
+            if (lane == 0)
+                sm.gsum[w] = __popc(bal);
+            bar_sync_named(1, RADIX);
+            u32 before = __popc(bal & lanemask_lt());
+            for (u32 i = 0; i < w; ++i)
+                before += sm.gsum[i];
+            if (head)
+                sm.glist[before] = (unsigned short)tid;
+            if (tid == RADIX - 1) {
+                const u32 ng = before + (head ? 1u : 0u);
+                sm.ngroups = ng;
+                sm.glist[ng] = RADIX;
+            }
+        }
+        __syncthreads();
+        const u32 ngroups = sm.ngroups;
+        for (u32 g = 0; g < ngroups; ++g) {
+            const u32 d0 = sm.glist[g], d1 = sm.glist[g + 1];
+            const u32 ga = sm.cbeg[d0], gb = sm.cbeg[d1];
+            const u32 m = gb - ga, c0 = sm.cbeg[d0 + 1] - ga;
+            if (m == 0 || c0 > CAP)
+                continue;  // empty, or left to the next level
+            const u64 *gsrc = stg + (u64)ga * rw;
+            u64 *recs = buf0 + (((item.begin + ga) * rw) & 1u);
+            load_words_async<THREADS>(recs, gsrc, (u64)m * rw);
+            cp_async_commit();
+            cp_async_wait<0>();
+            if (tid == 0)
+                sm.b.big_group = 0;
+            __syncthreads();
+            u64 *gout = out + (u64)ga * rw;
+            if (c0 <= WARP_MAX) {
+                // a run of small sub-bins: one warp per sub-bin
+                varying_digits_below<THREADS, K>(sm.b, recs, rw, m, p_word, t1 % 8u, key_words);
+                const u32 nv = sm.b.nv;
+                for (u32 ci = d0 + w; ci < d1; ci += NW) {
+                    const u32 cb = sm.cbeg[ci] - ga, cc = sm.cbeg[ci + 1] - sm.cbeg[ci];
+                    if (cc == 0)
+                        continue;
+                    warp_sort_bin<RW>(sm.b.rank.cnt[w], sm.b.xidx, sm.b.xcode, sm.b.xnew, recs, rw, cb, cc,
+                                      sm.b.vword, sm.b.vshift, nv, p_word, key_words, gout);
+                }
+            } else {
+                // one sub-bin of up to CAP records: the whole CTA
+                u32 id[K];
+                const u32 kv = (m + THREADS - 1) / THREADS;
+                block_path<THREADS, K>(sm.b, recs, rw, m, kv, t1 - 1u, key_words, id);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
+                    if ((u32)k < kv && pos < m)
+                        copy_record<RW>(gout + (u64)pos * rw, recs + (u64)id[k] * rw, rw);
+                }
+            }
+            __syncthreads();
+            if (!from_tmp)  // the group's scratch copy is dead: drop it from L2 unwritten
+                discard_range<THREADS>(gsrc, gsrc + (u64)m * rw);
+        }
+        __syncthreads();
+    }
+}
+
+namespace {
+
+// mid-size bin variants: {id, threads, K (group = threads*K), KS (chunk = threads*KS), RW}
+#define BUCKET_VARIANTS(X) \
+    X(0, 1024, 8, 4, 1)    \
+    X(1, 1024, 8, 4, 2)    \
+    X(2, 1024, 4, 2, 4)
+
+template <int THREADS, int K, int KS, int RW>
+cudaError_t launch_bucket_t(u64 *in, u64 *tmp, const PlanArgs &a, cudaStream_t st)
+{
+    const u32 sms = bucket_grid();
+    const size_t code_smem = round16b(sizeof(BucketCommon<THREADS>)) + sizeof(BucketCodeSmem);
+    cudaError_t e = cudaFuncSetAttribute(bucket_kernel<THREADS, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)code_smem);
+    if (e != cudaSuccess)
+        return e;
+    bucket_kernel<THREADS, RW><<<sms, THREADS, code_smem, st>>>(in, tmp, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const size_t split_smem = round16b(sizeof(BucketSplitSmem<THREADS, K, KS>)) +
+                              bucket_buf_words<THREADS, K, KS>((u32)RW) * 8;
+    e = cudaFuncSetAttribute(bucket_split_kernel<THREADS, K, KS, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)split_smem);
+    if (e != cudaSuccess)
+        return e;
+    bucket_split_kernel<THREADS, K, KS, RW><<<sms, THREADS, split_smem, st>>>(in, tmp, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+u32 bucket_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (u32)(sms > 0 ? sms : 1);
+}
+
+cudaError_t launch_bucket(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, cudaStream_t st)
+{
+    switch (s.bucket_var) {
+#define X(v, T, K, KS, RW) \
+    case v:                \
+        return launch_bucket_t<T, K, KS, RW>(in, tmp, a, st);
+        BUCKET_VARIANTS(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace raduls

@@ -60,13 +60,19 @@ struct Counters {
     u32 copy;             // copy-back items (cumulative)
     u32 copy_tiles;       // copy-back tiles (cumulative)
     u64 block;            // on-chip sort items (cumulative)
-    u32 tile_ctr[4];      // dynamic tile counters: 0 hist, 1 scatter, 2 copy, 3 block
+    u32 tile_ctr[5];      // dynamic tile counters: 0 hist, 1 scatter, 2 copy, 3 block, 4 mid-size bins
+    u32 bucket_cur;       // mid-size bins sorted by one CTA each in this level
+    u32 bucket_next;      // mid-size bins found in this level
+    u32 bucket_split;     // mid-size bins of this level left to the stable split
+    u32 split_ctr;        // dynamic item counter of the stable split
     u32 err;              // first device-detected error (ST_*)
     u32 grid_passes;      // distribution passes run
     u64 skipped;          // constant digits skipped
     u64 hist_bytes;       // algorithmic bytes read by histogram tiles
     u64 scatter_bytes;    // algorithmic bytes read+written by distribution tiles
     u64 block_bytes;      // bytes read+written by on-chip sorts and copies
+    u64 bucket_bytes;     // algorithmic bytes read+written by the mid-size bin kernel
+    u64 bucket_items;     // mid-size bins sorted (cumulative)
     u32 levels;
     u32 learned_ok;       // 1 while the learned partition passes its balance check
     float learned_ratio;  // max bucket / ideal bucket of the learned partition (0 = not measured)
@@ -74,6 +80,9 @@ struct Counters {
 };
 
 // Capacities of the device lists (set by the host from n and the tile sizes).
+// Largest mid-size bin (records): positions inside it are 16-bit.
+constexpr u32 BUCKET_IDX_MAX = 40960;
+
 struct Caps {
     u32 grid;       // grid list items (per level)
     u32 hist_tiles; // histogram tiles per level
@@ -303,6 +312,29 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, u32 by
                  : "memory");
 }
 
+// Asynchronous 16-byte copy global -> shared that bypasses L1 (cp.async.cg,
+// cached in L2 only); completes with cp_async_wait.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Drop the 128-byte L2 line at `p` (128-byte aligned) without writing it back:
+// its contents become undefined.  Only for lines whose data is dead.
+__device__ __forceinline__ void discard_l2_line(const void *p)
+{
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 __device__ __forceinline__ void set_error(Counters *c, u32 code)
 {
     atomicCAS(&c->err, 0u, code);
@@ -365,6 +397,34 @@ __device__ __forceinline__ void load_words(u64 *__restrict__ s, const u64 *__res
     } else {
         for (u64 i = tid; i < nwords; i += THREADS)
             s[i] = __ldcs(g + i);
+    }
+}
+
+// Asynchronous form of load_words (same layout rule): the 16-byte body moves
+// with cp.async.cg (through L2 only, never a stale L1 line); at most two edge
+// words are loaded directly.  The caller commits and waits.
+template <int THREADS>
+__device__ __forceinline__ void load_words_async(u64 *__restrict__ s, const u64 *__restrict__ g, u64 nwords)
+{
+    const u32 tid = threadIdx.x;
+    if (((((uintptr_t)g) ^ ((uintptr_t)s)) & 15u) == 0) {
+        if ((((uintptr_t)g) & 15u) != 0 && nwords > 0) {
+            if (tid == 0)
+                s[0] = __ldcg(g);
+            ++g;
+            ++s;
+            --nwords;
+        }
+        const u64 nv = nwords >> 1;
+        const uint4 *gv = reinterpret_cast<const uint4 *>(g);
+        uint4 *sv = reinterpret_cast<uint4 *>(s);
+        for (u64 i = tid; i < nv; i += THREADS)
+            cp_async16(sv + i, gv + i);
+        if ((nwords & 1) && tid == 0)
+            s[nwords - 1] = __ldcg(g + nwords - 1);
+    } else {
+        for (u64 i = tid; i < nwords; i += THREADS)
+            s[i] = __ldcg(g + i);
     }
 }
 

@@ -53,6 +53,16 @@ Shape choose_shape(u32 rw, u32 key_words)
     }
     s.tile_s = scatter_tile_of(s.scat_var);
     s.cap_b = block_cap_of(s.block_var);
+    // mid-size bins: one CTA splits a bin of up to BUCKET_BYTES through L2
+    constexpr u32 BUCKET_BYTES = 640u * 1024u;
+    s.bucket_var = rw == 1 ? 0 : rw == 2 ? 1 : rw == 4 ? 2 : -1;
+    s.bucket_max = s.bucket_var < 0 ? 0u : BUCKET_BYTES / (rw * 8u);
+    if (const char *v = getenv("RADULS_BUCKET_MAX"))
+        s.bucket_max = s.bucket_var < 0 ? 0u : (u32)strtoul(v, nullptr, 10);
+    if (s.bucket_max > BUCKET_IDX_MAX)  // positions inside a mid-size bin are 16-bit
+        s.bucket_max = BUCKET_IDX_MAX;
+    if (s.bucket_max <= s.cap_b)
+        s.bucket_max = 0;
     return s;
 }
 
@@ -72,6 +82,7 @@ struct Work {
     Counters *h_ctrs = nullptr;  // pinned host mirror
     u32 *epoch = nullptr;        // device: look-back epoch of the last distribution launch, wrap flag
     DevBuf lists, hist, status, tiles;
+    DevBuf bscratch;  // private scratch regions of the mid-size bin kernel's CTAs
 };
 
 // Device buffers of one learned model (see the Model struct in common.cuh).
@@ -138,6 +149,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Lists {
     WorkItem *grid[2];
     WorkItem *scat;
+    WorkItem *bkt[2];
+    WorkItem *bkt_split;
     WorkItem *blocks;
     WorkItem *copies;
     u32 *tile_hist;
@@ -233,10 +246,13 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
         block_cap = n + 4;
     if (grid_cap > 0xffffffffull || hist_tiles > 0xffffffffull || copy_tiles > 0xffffffffull)
         return cudaErrorInvalidValue;
-    size_t off = 0, o_grid0, o_grid1, o_scat, o_blocks, o_copies, o_th, o_tc;
+    size_t off = 0, o_grid0, o_grid1, o_scat, o_bkt0, o_bkt1, o_bkts, o_blocks, o_copies, o_th, o_tc;
     o_grid0 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_grid1 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_scat = off; off = align256(off + grid_cap * sizeof(WorkItem));
+    o_bkt0 = off; off = align256(off + grid_cap * sizeof(WorkItem));
+    o_bkt1 = off; off = align256(off + grid_cap * sizeof(WorkItem));
+    o_bkts = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_blocks = off; off = align256(off + block_cap * sizeof(WorkItem));
     o_copies = off; off = align256(off + copy_cap * sizeof(WorkItem));
     o_th = off; off = align256(off + hist_tiles * 4);
@@ -248,6 +264,9 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
     L.grid[0] = (WorkItem *)(b + o_grid0);
     L.grid[1] = (WorkItem *)(b + o_grid1);
     L.scat = (WorkItem *)(b + o_scat);
+    L.bkt[0] = (WorkItem *)(b + o_bkt0);
+    L.bkt[1] = (WorkItem *)(b + o_bkt1);
+    L.bkt_split = (WorkItem *)(b + o_bkts);
     L.blocks = (WorkItem *)(b + o_blocks);
     L.copies = (WorkItem *)(b + o_copies);
     L.tile_hist = (u32 *)(b + o_th);
@@ -506,8 +525,11 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
     const u32 top = 8u * j.kw - 1u;
     const bool step_api = j.single_pass || j.hist_out;
     const bool may_learn = !step_api && j.mode != 1 && j.n > s.cap_b;
+    const u32 bmax = step_api ? 0u : s.bucket_max;
+    if (bmax)
+        CK(ensure(wk.bscratch, (size_t)bucket_grid() * bmax * j.rw * 8, false));
     TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, step_api ? j.digit : top,
-                                      s.cap_b, s.tile_h, step_api ? 1u : 0u, st));
+                                      s.cap_b, s.tile_h, step_api ? 1u : 0u, L.bkt[0], bmax, st));
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
         c.wait_ns = g_wait_ns;
@@ -517,57 +539,17 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
     bool learned = false;
     float ratio_limit = j.fallback_ratio > 0.f ? j.fallback_ratio : 4.f;
     int cur = 0;
-    u32 n_grid = (step_api || j.n > s.cap_b) ? 1u : 0u;
-    for (u32 level = 0; n_grid > 0; ++level) {
-        LevelBufs B{};
-        CK(work_level(wk, s, j.n, n_grid, B, L.caps, st));
-        const Model *model = learned ? c.mdl.model : nullptr;
-        TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
-        TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
-                                         wk.ctrs, model, st));
-        if (j.hist_out) {
-            CK(cudaMemcpyAsync(j.hist_out, B.hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
-            break;
-        }
-        if (level == 0 && may_learn) {
-            // the first pass's digit histogram decides (auto) and is the model's root
-            bool use = (j.mode == 2);
-            if (!use) {
-                u64 h[RADIX];
-                CK(cudaMemcpyAsync(h, B.hist, sizeof h, cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                u64 mx = 0;
-                for (int d = 0; d < RADIX; ++d)
-                    mx = h[d] > mx ? h[d] : mx;
-                use = mx > 4ull * (j.n / RADIX) && j.kw >= 1;
-            }
-            if (use) {
-                const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
-                int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);
-                if (rc)
-                    return rc;
-                learned = true;
-                // restart the level on the model's top digit
-                TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, DIGIT_LEARNED_HI,
-                                                  s.cap_b, s.tile_h, 1u, st));
-                TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
-                TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand,
-                                                 B.dlight, wk.ctrs, c.mdl.model, st));
-                model = c.mdl.model;
-            }
-        }
-        if (learned && level == 1)
-            TIMED(RADULS_K_LEARNED, lm_launch_ratio(B.dlight, wk.ctrs, c.mdl.model, ratio_limit, st));
+    const bool whole_mid = !step_api && j.n > s.cap_b && j.n <= bmax;
+    u32 n_grid = (step_api || (j.n > s.cap_b && !whole_mid)) ? 1u : 0u;
+    u32 n_bkt = whole_mid ? 1u : 0u;
+    for (u32 level = 0; n_grid > 0 || n_bkt > 0; ++level) {
         PlanArgs a{};
         a.grid_cur = L.grid[cur];
         a.grid_next = L.grid[cur ^ 1];
         a.scat = L.scat;
         a.blocks = L.blocks;
         a.copies = L.copies;
-        a.hist = B.hist;
-        a.orand = B.orand;
         a.tile_hist = L.tile_hist;
-        a.tile_scat = B.tile_scat;
         a.tile_copy = L.tile_copy;
         a.ctrs = wk.ctrs;
         a.caps = L.caps;
@@ -580,11 +562,63 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         a.tile_c = s.tile_c;
         a.single_pass = j.single_pass ? 1u : 0u;
         a.top_digit = top;
-        TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-        TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
-        TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs,
-                                               wk.epoch, c.wait_ns, c.inject_tile, model, st));
-        c.inject_tile = ~0u;
+        a.buckets_cur = L.bkt[cur];
+        a.buckets_next = L.bkt[cur ^ 1];
+        a.buckets_split = L.bkt_split;
+        a.bucket_max = bmax;
+        a.bucket_scratch = (u64 *)wk.bscratch.p;
+        if (n_grid > 0) {
+            LevelBufs B{};
+            CK(work_level(wk, s, j.n, n_grid, B, L.caps, st));
+            a.caps = L.caps;  // the level's buffers fix the distribution tile capacity
+            const Model *model = learned ? c.mdl.model : nullptr;
+            TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
+            TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
+                                             wk.ctrs, model, st));
+            if (j.hist_out) {
+                CK(cudaMemcpyAsync(j.hist_out, B.hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
+                break;
+            }
+            if (level == 0 && may_learn) {
+                // the first pass's digit histogram decides (auto) and is the model's root
+                bool use = (j.mode == 2);
+                if (!use) {
+                    u64 h[RADIX];
+                    CK(cudaMemcpyAsync(h, B.hist, sizeof h, cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    u64 mx = 0;
+                    for (int d = 0; d < RADIX; ++d)
+                        mx = h[d] > mx ? h[d] : mx;
+                    use = mx > 4ull * (j.n / RADIX) && j.kw >= 1;
+                }
+                if (use) {
+                    const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
+                    int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);
+                    if (rc)
+                        return rc;
+                    learned = true;
+                    // restart the level on the model's top digit
+                    TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n,
+                                                      DIGIT_LEARNED_HI, s.cap_b, s.tile_h, 1u, nullptr, 0u, st));
+                    TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
+                    TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand,
+                                                     B.dlight, wk.ctrs, c.mdl.model, st));
+                    model = c.mdl.model;
+                }
+            }
+            if (learned && level == 1)
+                TIMED(RADULS_K_LEARNED, lm_launch_ratio(B.dlight, wk.ctrs, c.mdl.model, ratio_limit, st));
+            a.hist = B.hist;
+            a.orand = B.orand;
+            a.tile_scat = B.tile_scat;
+            TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
+            TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+            TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs,
+                                                   wk.epoch, c.wait_ns, c.inject_tile, model, st));
+            c.inject_tile = ~0u;
+        }
+        if (n_bkt > 0)
+            TIMED(RADULS_K_BUCKET, launch_bucket(s, j.in, j.tmp, a, st));
         TIMED(RADULS_K_SETUP, launch_advance(wk.ctrs, st));
         if (j.single_pass)
             break;
@@ -593,6 +627,7 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         if (wk.h_ctrs->err)
             break;
         n_grid = wk.h_ctrs->grid_cur;
+        n_bkt = wk.h_ctrs->bucket_cur;
         cur ^= 1;
     }
     if (!step_api) {
@@ -619,6 +654,8 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         o.learned_fell_back = learned ? h.learned_fell_back : 0u;
         o.learned_ratio = learned ? h.learned_ratio : 0.f;
         o.gpu_launches = rec.total;
+        o.bucket_items = h.bucket_items;
+        o.bucket_bytes = h.bucket_bytes;
         for (int k = 0; k < RADULS_K_COUNT; ++k) {
             o.kernel_launches[k] = rec.launches[k];
             o.kernel_ms[k] = 0.f;
@@ -649,6 +686,7 @@ struct BatchGraph {
     const void *off = nullptr;
     u64 n = 0;
     u32 n_segs = 0, rw = 0, kw = 0;
+    void *ws[5] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
 };
 
 BatchGraph g_batch[MAX_DEVICES];
@@ -658,7 +696,7 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
 {
     const u32 top = 8u * kw - 1u;
     CK(launch_batched_init(off, n_segs, L.grid[0], L.blocks, L.tile_hist, wk.ctrs, L.caps, top, s.cap_b, s.tile_h,
-                           st));
+                           L.bkt[0], s.bucket_max, st));
     int cur = 0;
     const u32 levels = 8u * kw;
     for (u32 level = 0; level < levels; ++level) {
@@ -686,13 +724,21 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
         a.tile_c = s.tile_c;
         a.single_pass = 0;
         a.top_digit = top;
+        a.buckets_cur = L.bkt[cur];
+        a.buckets_next = L.bkt[cur ^ 1];
+        a.buckets_split = L.bkt_split;
+        a.bucket_max = s.bucket_max;
+        a.bucket_scratch = (u64 *)wk.bscratch.p;
         CK(launch_plan(a, 0, st));
         CK(launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
         CK(launch_scatter(s, in, tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs, wk.epoch, c.wait_ns, ~0u,
                           nullptr, st));
+        if (a.bucket_max)
+            CK(launch_bucket(s, in, tmp, a, st));
         CK(launch_advance(wk.ctrs, st));
         cur ^= 1;
     }
+    CK(launch_check_drained(wk.ctrs, st));
     CK(launch_copy(s, in, tmp, L.copies, L.tile_copy, wk.ctrs, st));
     CK(launch_block_sort(s, in, tmp, L.blocks, wk.ctrs, off, st));
     fold_status_kernel<<<1, 1, 0, st>>>(wk.ctrs, c.dev_status);
@@ -710,13 +756,19 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
     CK(work_lists(wk, s, n + 2ull * n_segs + 2ull * s.cap_b, L));
     LevelBufs B{};
     CK(work_level(wk, s, n, L.caps.grid, B, L.caps, st));
+    if (s.bucket_max)
+        CK(ensure(wk.bscratch, (size_t)bucket_grid() * s.bucket_max * rw * 8, false));
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
         c.wait_ns = g_wait_ns;
     }
     BatchGraph &bg = g_batch[dev];
+    void *const ws[5] = {wk.lists.p, wk.hist.p, wk.status.p, wk.tiles.p, wk.bscratch.p};
+    bool same_ws = true;
+    for (int i = 0; i < 5; ++i)
+        same_ws = same_ws && bg.ws[i] == ws[i];
     const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
-                     bg.rw == rw && bg.kw == kw && bg.in != nullptr;
+                     bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws;
     if (!hit) {
         if (bg.exec) {
             cudaGraphExecDestroy(bg.exec);
@@ -745,6 +797,8 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         bg.n_segs = n_segs;
         bg.rw = rw;
         bg.kw = kw;
+        for (int i = 0; i < 5; ++i)
+            bg.ws[i] = ws[i];
     }
     CK(cudaGraphLaunch(bg.exec, st));
     return RADULS_OK;

@@ -13,8 +13,10 @@ struct Shape {
     u32 tile_s;      // records per distribution tile
     u32 tile_c;      // records per copy tile
     u32 cap_b;       // largest bin sorted on chip
+    u32 bucket_max;  // largest bin split and sorted by one CTA through L2 (0: none)
     int scat_var;    // distribution kernel variant
     int block_var;   // on-chip sort kernel variant
+    int bucket_var;  // mid-size bin kernel variant (-1: none for this record width)
 };
 
 Shape choose_shape(u32 rw, u32 key_words);
@@ -55,16 +57,78 @@ struct PlanArgs {
     u32 tile_h, tile_s, tile_c;
     u32 single_pass;  // 1: distribute every item once, no children (single-step API)
     u32 top_digit;    // most significant key digit (8 * key_words - 1)
+    WorkItem *buckets_cur;   // mid-size bins sorted by one CTA each in this level
+    WorkItem *buckets_next;  // mid-size bins found in this level (sorted in the next one)
+    WorkItem *buckets_split; // mid-size bins of this level with heavy code groups (stable split)
+    u32 bucket_max;          // bins of plain digits with count <= bucket_max go there (0: never)
+    u64 *bucket_scratch;     // bucket_max * rw words per CTA of the mid-size bin kernel
 };
 
+// CTAs of the mid-size bin kernel (one per SM): its scratch holds that many regions.
+u32 bucket_grid();
+
+__device__ __forceinline__ u32 ceil_div_u64(u64 a, u32 b) { return (u32)((a + b - 1) / b); }
+
+// Append a bin to the next grid list and map its histogram tiles.
+__device__ __forceinline__ void append_grid(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+{
+    const u32 slot = atomicAdd(&a.ctrs->grid_next, 1u);
+    const u32 nt = ceil_div_u64(count, a.tile_h);
+    const u32 tb = atomicAdd(&a.ctrs->grid_next_tiles, nt);
+    if (slot >= a.caps.grid || (u64)tb + nt > a.caps.hist_tiles) {
+        set_error(a.ctrs, ST_INTERNAL);
+        return;
+    }
+    WorkItem it;
+    it.begin = begin;
+    it.count = count;
+    it.digit = digit;
+    it.flags = flags;
+    it.tile_base = tb;
+    it.row = slot;
+    a.grid_next[slot] = it;
+    for (u32 j = 0; j < nt; ++j)
+        a.tile_hist[tb + j] = slot;
+}
+
+// Append a bin that still needs sorting from digit `digit` down: a mid-size
+// bin of a plain digit goes to the next level's mid-size list (no histogram
+// pass: its kernel counts for itself), any other to the next grid list.
+__device__ __forceinline__ void append_bin(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+{
+    if (a.bucket_max && digit < DIGIT_LEARNED_HI && count <= a.bucket_max) {
+        const u32 slot = atomicAdd(&a.ctrs->bucket_next, 1u);
+        if (slot >= a.caps.grid) {
+            set_error(a.ctrs, ST_INTERNAL);
+            return;
+        }
+        WorkItem it;
+        it.begin = begin;
+        it.count = count;
+        it.digit = digit;
+        it.flags = flags;
+        it.tile_base = 0;
+        it.row = 0;
+        a.buckets_next[slot] = it;
+        return;
+    }
+    append_grid(a, begin, count, digit, flags);
+}
+
+// Mid-size bins (bucketsort.cu): every bin of a.buckets_cur is sorted by one
+// CTA that reads it from HBM once and keeps its scratch copy in L2.
+cudaError_t launch_bucket(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, cudaStream_t st);
+
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
-                        u32 cap_b, u32 tile_h, u32 force_grid, cudaStream_t st);
+                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, cudaStream_t st);
 cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint,
                         cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
-                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, cudaStream_t st);
+                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
+                                u32 bucket_max, cudaStream_t st);
+cudaError_t launch_check_drained(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st);
 cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,
                         Counters *ctrs, cudaStream_t st);

@@ -10,35 +10,13 @@
 //     records that one CTA sorts on chip (the "small"/"tiny" bins of Sec. 3.4
 //     and 3.5, Fig. 3);
 //   * no digits left but still in the scratch buffer -> copied back.
+// A bin small enough for one CTA to sort through L2 (bucket_max) goes to the
+// mid-size list instead of the next grid list (bucketsort.cu).
 // A bin whose digit is the same for all its records is not distributed: it
 // moves on to its next varying digit without any data movement.
 #include "kernels.h"
 
 namespace raduls {
-
-__device__ __forceinline__ u32 ceil_div_u64(u64 a, u32 b) { return (u32)((a + b - 1) / b); }
-
-// Append a bin to the next grid list and map its histogram tiles.
-__device__ void append_grid(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
-{
-    const u32 slot = atomicAdd(&a.ctrs->grid_next, 1u);
-    const u32 nt = ceil_div_u64(count, a.tile_h);
-    const u32 tb = atomicAdd(&a.ctrs->grid_next_tiles, nt);
-    if (slot >= a.caps.grid || (u64)tb + nt > a.caps.hist_tiles) {
-        set_error(a.ctrs, ST_INTERNAL);
-        return;
-    }
-    WorkItem it;
-    it.begin = begin;
-    it.count = count;
-    it.digit = digit;
-    it.flags = flags;
-    it.tile_base = tb;
-    it.row = slot;
-    a.grid_next[slot] = it;
-    for (u32 j = 0; j < nt; ++j)
-        a.tile_hist[tb + j] = slot;
-}
 
 __device__ void append_copy(const PlanArgs &a, u64 begin, u64 count)
 {
@@ -123,7 +101,7 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
             // the learned partition failed its balance check: this bin goes on
             // with plain key digits (its top-8-bit model split stays valid)
             if (d == 0)
-                append_grid(a, it.begin, it.count, a.top_digit, it.flags);
+                append_bin(a, it.begin, it.count, a.top_digit, it.flags);
             __syncthreads();
             continue;
         }
@@ -135,7 +113,7 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
                 if (np >= 0) {
                     if (!learned)
                         atomicAdd(&a.ctrs->skipped, (u64)(p - (u32)np));
-                    append_grid(a, it.begin, it.count, (u32)np, it.flags);
+                    append_bin(a, it.begin, it.count, (u32)np, it.flags);
                 } else {
                     atomicAdd(&a.ctrs->skipped, (u64)(p + 1));
                     if (it.flags & ITEM_IN_TMP)
@@ -194,7 +172,7 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
         s_big[d] = big ? 1 : 0;
         if (big) {
             if (cd >= 0)
-                append_grid(a, it.begin + ex, h, (u32)cd, cflags);
+                append_bin(a, it.begin + ex, h, (u32)cd, cflags);
             else if (cflags & ITEM_IN_TMP)
                 append_copy(a, it.begin + ex, h);
         }
@@ -238,14 +216,19 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
 }
 
 __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top,
-                            u32 cap_b, u32 tile_h, u32 force_grid)
+                            u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max)
 {
     const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool grid = force_grid || n > cap_b;
+    const bool mid = !force_grid && n > cap_b && n <= bucket_max;
+    const bool grid = !mid && (force_grid || n > cap_b);
     const u32 nt = grid ? (u32)((n + tile_h - 1) / tile_h) : 0u;
     if (i == 0) {
         Counters c = {};
-        if (grid) {
+        if (mid) {
+            WorkItem it = {0ull, n, top, 0u, 0u, 0u};
+            bucket0[0] = it;
+            c.bucket_cur = 1;
+        } else if (grid) {
             WorkItem it = {0ull, n, top, 0u, 0u, 0u};
             grid0[0] = it;
             c.grid_cur = 1;
@@ -288,6 +271,11 @@ __global__ void advance_kernel(Counters *c)
     c->scatter_tiles = 0;
     c->tile_ctr[0] = 0;
     c->tile_ctr[1] = 0;
+    c->bucket_cur = c->bucket_next;
+    c->bucket_next = 0;
+    c->bucket_split = 0;
+    c->split_ctr = 0;
+    c->tile_ctr[4] = 0;
 }
 
 template <int THREADS>
@@ -339,7 +327,7 @@ __global__ void batched_validate_kernel(const u64 *__restrict__ off, u32 n_segs,
 // most 256 arrays), sorted one warp per array.
 __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs, WorkItem *grid0, WorkItem *blocks,
                                         u32 *tile_hist, Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 warp_bin,
-                                        u32 tile_h, u32 win)
+                                        u32 tile_h, u32 win, WorkItem *bucket0, u32 bucket_max)
 {
     if (ctrs->err)
         return;
@@ -347,7 +335,15 @@ __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs,
     auto key = [&](u32 s) { return (off[s] / win) * 1048576ull + (s >> 8); };
     for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x) {
         const u64 a = off[s], c = off[s + 1] - a;
-        if (c > cap_b) {
+        if (c > cap_b && c <= bucket_max) {
+            const u32 slot = atomicAdd(&ctrs->bucket_cur, 1u);
+            if (slot >= caps.grid) {
+                set_error(ctrs, ST_INTERNAL);
+                continue;
+            }
+            WorkItem it = {a, c, top, 0u, 0u, 0u};
+            bucket0[slot] = it;
+        } else if (c > cap_b) {
             const u32 slot = atomicAdd(&ctrs->grid_cur, 1u);
             const u32 nt = (u32)((c + tile_h - 1) / tile_h);
             const u32 tb = atomicAdd(&ctrs->grid_cur_tiles, nt);
@@ -385,14 +381,28 @@ __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs,
     }
 }
 
+// After the last level nothing may be left unsorted.
+__global__ void check_drained_kernel(Counters *ctrs)
+{
+    if (ctrs->grid_cur != 0 || ctrs->bucket_cur != 0)
+        set_error(ctrs, ST_INTERNAL);
+}
+
+cudaError_t launch_check_drained(Counters *ctrs, cudaStream_t st)
+{
+    check_drained_kernel<<<1, 1, 0, st>>>(ctrs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
-                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, cudaStream_t st)
+                                Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
+                                u32 bucket_max, cudaStream_t st)
 {
     batched_reset_kernel<<<1, 1, 0, st>>>(ctrs);
     const u32 blocks_n = n_segs / 256 + 1 < 4096 ? n_segs / 256 + 1 : 4096;
     batched_validate_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, ctrs);
     batched_classify_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, grid0, blocks, tile_hist, ctrs, caps, top, cap_b,
-                                                      WARP_BIN, tile_h, cap_b - WARP_BIN);
+                                                      WARP_BIN, tile_h, cap_b - WARP_BIN, bucket0, bucket_max);
     return cudaGetLastError();
 }
 
@@ -425,9 +435,10 @@ cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st)
 }
 
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
-                        u32 cap_b, u32 tile_h, u32 force_grid, cudaStream_t st)
+                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, cudaStream_t st)
 {
-    init_kernel<<<256, 256, 0, st>>>(ctrs, grid0, blocks, tile_hist, n, top_digit, cap_b, tile_h, force_grid);
+    init_kernel<<<256, 256, 0, st>>>(ctrs, grid0, blocks, tile_hist, n, top_digit, cap_b, tile_h, force_grid, bucket0,
+                                     bucket_max);
     return cudaGetLastError();
 }
 
