@@ -7,10 +7,11 @@ each timed step the input is restored from a pristine device copy (untimed);
 the 32 GiB input is far larger than the 129 MB L2, so no step starts warm.
 
 Reported next to records/s:
-  * roofline -- the dominant kernel (the distribution pass): algorithmic bytes
-    per launch (read + write of every record it moves) over its launch time
-    measured live with CUDA events recorded by the library on the launching
-    stream, against the measured HBM copy bandwidth;
+  * roofline -- the dominant kernel (the class with the most device time per
+    step): algorithmic bytes per launch (read + write of every record it
+    moves) over its launch time measured live with CUDA events recorded by the
+    library on the launching stream, against the measured HBM copy bandwidth;
+    every class's figure is listed under roofline.per_kernel;
   * cpu_baseline -- the CPU oracle (LSD counting sort) on a bounded sample of
     the same workload on this host's cores;
   * e2e -- the same metric with the records in pinned host memory, the
@@ -58,10 +59,21 @@ WORKLOADS = {
                            "on a prefix of the arrays timed alongside)", n=0, rec=16, key=8, mode="batched"),
 }
 
-# ncu DRAM traffic of one distribution launch, per record moved, measured on
-# the uniform 16-byte workload (profiles/scatter_uniform16.md); None until taken
-# for the current kernel.
-SCATTER_DRAM_BYTES_PER_RECORD = None
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record
+# moved, per kernel class, from one capture of the current kernels on uniform
+# 16-byte records (profiles/).  A class missing here has no capture of
+# its current code.
+DRAM_BYTES_PER_RECORD = {
+    "scatter": (1.096104e9 + 1.048388e9) / 2 ** 26,   # profiles/scatter_uniform16.md (2^26 records)
+    "bucket": (533.259776e6 + 401.044224e6) / 1e7,    # profiles/bucket_uniform16.md (10^7 records)
+}
+# stats field holding each class's algorithmic bytes (read + write of every record it moves)
+CLASS_BYTES = {"scatter": "scatter_bytes", "bucket": "bucket_bytes", "block": "block_bytes",
+               "hist": "hist_bytes_read"}
+CLASS_KERNEL = {"scatter": "scatter_kernel (MSD distribution pass of big bins)",
+                "bucket": "bucket_kernel (mid-size bins, one CTA each)",
+                "block": "block_sort_kernel (on-chip sorts of small bins)",
+                "hist": "hist_kernel (digit histograms of big bins)"}
 
 
 def peaks():
@@ -320,8 +332,8 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     step_ms = []
-    scat_ms = scat_launches = 0.0
-    scat_bytes = 0
+    cls_bytes = {c: 0 for c in CLASS_BYTES}
+    cls_launches = {c: 0 for c in CLASS_BYTES}
     launches = 0
     total_bytes = 0
     kernel_ms = {}
@@ -340,11 +352,11 @@ def main():
         step_ms.append(ev0.elapsed_time(ev1))
         if st is None:
             continue
-        scat_ms += st["kernel_ms"]["scatter"]
-        scat_launches += st["kernel_launches"]["scatter"]
-        scat_bytes += st["scatter_bytes"]
+        for c, field in CLASS_BYTES.items():
+            cls_bytes[c] += st[field]
+            cls_launches[c] += st["kernel_launches"][c]
         launches += st["gpu_launches"]
-        total_bytes += st["hist_bytes_read"] + st["scatter_bytes"] + st["block_bytes"]
+        total_bytes += st["hist_bytes_read"] + st["scatter_bytes"] + st["block_bytes"] + st["bucket_bytes"]
         for k, v in st["kernel_ms"].items():
             kernel_ms[k] = kernel_ms.get(k, 0.0) + v
         if st.get("learned_used"):
@@ -378,7 +390,8 @@ def main():
             cms.append(e0.elapsed_time(e1))
         comparison = {"plain_records_per_s": n * len(cms) / (sum(cms) / 1e3),
                       "plain_ms_per_step": sum(cms) / len(cms),
-                      "plain_bytes_moved": cst["hist_bytes_read"] + cst["scatter_bytes"] + cst["block_bytes"],
+                      "plain_bytes_moved": (cst["hist_bytes_read"] + cst["scatter_bytes"] + cst["block_bytes"]
+                                            + cst["bucket_bytes"]),
                       "learned_bytes_moved": total_bytes // max(args.steps, 1),
                       "learned_speedup": (sum(cms) / len(cms)) / (tot_ms / args.steps)}
     elif mode == "batched":
@@ -428,17 +441,29 @@ def main():
                "ms_per_step": et / args.e2e_steps}
         del host_out
 
-    achieved = (scat_bytes / (scat_ms / 1e3)) / 1e9 if scat_ms > 0 else None
+    # per kernel class: algorithmic bytes over its CUDA-event time; the
+    # dominant class (most time per step) is the roofline's kernel
+    per_kernel = {}
+    for c in CLASS_BYTES:
+        ms = kernel_ms.get(c, 0.0)
+        if ms > 0 and cls_launches[c] > 0:
+            gbs = cls_bytes[c] / (ms / 1e3) / 1e9
+            per_kernel[c] = {"ms_per_step": ms / args.steps, "launches_per_step": cls_launches[c] / args.steps,
+                             "gbs": gbs, "frac": gbs / hbm_peak}
+    dom = max(per_kernel, key=lambda c: per_kernel[c]["ms_per_step"]) if per_kernel else "scatter"
+    dom_ms, dom_launches, dom_bytes = kernel_ms.get(dom, 0.0), cls_launches[dom], cls_bytes[dom]
+    achieved = (dom_bytes / (dom_ms / 1e3)) / 1e9 if dom_ms > 0 else None
     traffic = None
-    if SCATTER_DRAM_BYTES_PER_RECORD is not None and scat_launches:
-        traffic = SCATTER_DRAM_BYTES_PER_RECORD * (scat_bytes / (2 * rec)) / scat_launches
+    if dom in DRAM_BYTES_PER_RECORD and dom_launches and dom != "hist":
+        traffic = DRAM_BYTES_PER_RECORD[dom] * (dom_bytes / (2 * rec)) / dom_launches
     roofline = {
-        "bound": "hbm", "kernel": "scatter_kernel (MSD distribution pass)",
+        "bound": "hbm", "kernel": CLASS_KERNEL[dom],
         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
         "frac": (achieved / hbm_peak) if achieved else None,
         "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-        "algorithmic_bytes_per_launch": scat_bytes / max(scat_launches, 1),
-        "launch_ms_avg": scat_ms / max(scat_launches, 1),
+        "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
+        "launch_ms_avg": dom_ms / max(dom_launches, 1),
+        "per_kernel": per_kernel,
         "whole_sort_gbs": total_bytes / (tot_ms / 1e3) / 1e9 / world if tot_ms else None,
         "whole_sort_frac": (total_bytes / (tot_ms / 1e3) / 1e9 / world) / hbm_peak if tot_ms else None,
         "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items() if v > 0},
