@@ -103,7 +103,7 @@ typedef struct {
                                        histogram is skewed), 1 PLAIN, 2 LEARNED */
     uint32_t learned_log2_buckets;  /* 12..16, 0 = chosen from n */
     float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio; 0 = 4.0 */
-    uint32_t train_steps;           /* Adam steps of the model fit; 0 = 100 */
+    uint32_t train_steps;           /* Adam steps per stage of the model fit; 0 = 16 */
     raduls_stats *stats;            /* host pointer or NULL */
 } raduls_opts;
 

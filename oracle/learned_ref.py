@@ -8,13 +8,16 @@ plain numpy in float64, written from the model's definition:
 * Root (level 1): the exact histogram R_j of the top byte j of key word 0
   over all records (the first MSD pass's digit histogram, Sec. 1 / Fig. 1),
   with exclusive prefix C_j.
-* Leaf (level 2), one per root segment j: the in-segment coordinate
-  t = fp32(word0 mod 2^56) * 2^-56 in [0, 1) goes through two
-  piecewise-linear stages u = f2(f1(t)); each stage maps its input through
-  knots (x_i, h_i), i = 0..m_j-1.  The knot positions x_i
-  are fixed (the GPU model spaces them uniformly over the range of the
-  segment's sample; knots_from_segments writes them out); the heights are h_0 = 0 and
-  h_i = sum_{l<i} softplus(theta_l) / sum_l softplus(theta_l), so h is
+* Leaf (level 2), one per root segment j: two piecewise-linear stages
+  u = f2(f1(key)); each stage maps its input through knots (x_i, h_i),
+  i = 0..m_j-1.  Stage 1's input is the key's low 56 bits in units of its
+  knot spacing, g = (low - base_j) / 2^sh_j (stage1_coords), with knots at
+  g = 0, 1, ..., m-1: the GPU model puts them 2^sh_j apart from the
+  segment's first sample.  Stage 2's input is f1's output in [0, 1] with
+  uniform knots.  knots_from_segments writes the knot positions out.  (The
+  generic functions below also accept t = fp32(word0 mod 2^56) * 2^-56 as
+  the default input, for synthetic knot layouts.)  The heights are h_0 = 0
+  and h_i = sum_{l<i} softplus(theta_l) / sum_l softplus(theta_l), so h is
   non-decreasing and ends at 1 by construction.
 * u(t) = 0 for t < x_0, 1 for t >= x_{m-1}, otherwise with i the last knot
   index in [0, m-2] with x_i <= t and lam = (t - x_i) / (x_{i+1} - x_i):
@@ -59,18 +62,37 @@ def split_keys(keys: np.ndarray):
     return j, t
 
 
-def knots_from_segments(seg) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """Explicit knot arrays of one stage of uniformly spaced leaves given per
-    segment as (x0, inv_w, first knot, knots, first parameter):
-    returns (knot_off relative to the stage, knot_x with x_i = x0 + i / inv_w,
-    parameter offsets)."""
+LOW56 = (1 << 56) - 1
+
+
+def stage1_coords(keys: np.ndarray, seg) -> np.ndarray:
+    """Stage-1 input of each key: g = (low - base_j) / 2^sh_j in float64, with
+    low = key mod 2^56 and j its top byte (exact integer difference; -1 below
+    the segment's first knot, where the stage's output is 0)."""
+    out = np.zeros(len(keys))
+    for idx, k in enumerate(np.asarray(keys, dtype=np.uint64).tolist()):
+        j = k >> 56
+        low, base, sh = k & LOW56, int(seg["base"][j]), int(seg["sh"][j])
+        out[idx] = -1.0 if low < base else float(low - base) / float(1 << sh)
+    return out
+
+
+def knots_from_segments(seg, stage: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Explicit knot arrays of one stage of the GPU model, given per segment as
+    (base, x0, inv_w, first knot, knots, first parameter, sh): returns
+    (knot_off relative to the stage, knot_x, parameter offsets).  Stage 0
+    (the first) has its knots at 0, 1, ..., m-1 of the stage1_coords scale;
+    stage 1 at x0 + i / inv_w."""
     m = np.asarray(seg["m"], dtype=np.int64)
     off = np.zeros(257, dtype=np.int64)
     off[1:] = np.cumsum(m)
     xs = np.zeros(int(off[-1]))
     for j in range(256):
         i = np.arange(m[j])
-        xs[off[j]:off[j + 1]] = float(seg["x0"][j]) + i / float(seg["inv_w"][j])
+        if stage == 0:
+            xs[off[j]:off[j + 1]] = i
+        else:
+            xs[off[j]:off[j + 1]] = float(seg["x0"][j]) + i / float(seg["inv_w"][j])
     return off, xs, np.asarray(seg["poff"], dtype=np.int64)
 
 

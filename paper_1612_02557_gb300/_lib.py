@@ -248,11 +248,11 @@ def raduls_set_wait_limit_ns(ns: int) -> None:
 class RaduLSModel:
     """Handle of a learned partition model fitted on the GPU (raduls_model_*)."""
 
-    SEG_DTYPE = [("x0", "<f4"), ("inv_w", "<f4"), ("koff", "<u4"), ("m", "<u4"), ("poff", "<u4"),
-                 ("pad", "<u4")]
+    SEG_DTYPE = [("base", "<u8"), ("x0", "<f4"), ("inv_w", "<f4"), ("koff", "<u4"), ("m", "<u4"),
+                 ("poff", "<u4"), ("sh", "<u4")]
 
     def __init__(self, in_, n_recs: int, rec_bytes: int, key_bytes: int, log2_buckets: int = 16,
-                 train_steps: int = 100, stream=None):
+                 train_steps: int = 16, stream=None):
         self._lib = load()
         self._h = ctypes.c_void_p()
         rc = self._lib.raduls_model_fit(ctypes.byref(self._h), _addr(in_), n_recs, rec_bytes, key_bytes,

@@ -257,56 +257,83 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
             const bool vq = two && (((o1 ^ a1) >> lb.sh) & 0xffu) != 0;
             cm.t1 = (vp && vq) ? (int)p : -2;  // -2: the speculation missed
             cm.t2 = (vp && vq) ? (int)p - 1 : -2;
-        }
-        __syncthreads();
-        if (cm.t1 == -2) {
-            // some of digits p, p-1 are constant here: find the bin's two most
-            // significant varying digits from the OR / AND of every key word
-            for (u32 wi = la.word; wi < key_words; ++wi) {
-                u64 vo = 0, va = ~0ull;
-                for (u32 i = tid; i < n; i += THREADS) {
-                    const u64 x = __ldcg(src + (u64)i * rw + wi);
-                    vo |= x;
-                    va &= x;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    vo |= __shfl_xor_sync(FULL_MASK, vo, o);
-                    va &= __shfl_xor_sync(FULL_MASK, va, o);
-                }
-                if (lane == 0) {
-                    cm.red_or[0][w] = vo;
-                    cm.red_and[0][w] = va;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    u64 o2 = 0, a2 = ~0ull;
-                    for (int i = 0; i < NW; ++i) {
-                        o2 |= cm.red_or[0][i];
-                        a2 &= cm.red_and[0][i];
-                    }
-                    u64 d = o2 ^ a2;
-                    if (wi == la.word && p % 8u != 7u)
-                        d &= (2ull << (8u * (p % 8u) + 7u)) - 1ull;  // bytes at or below digit p
-                    cm.diff[wi] = d;
-                }
-                __syncthreads();
-            }
-            if (tid == 0) {
+            if (!(vp && vq) && la.word == key_words - 1u) {
+                // every digit at or below p lies in this word: its OR / AND names
+                // the two most significant varying ones (-1: none)
+                u64 d = o0 ^ a0;
+                if (p % 8u != 7u)
+                    d &= (2ull << (8u * (p % 8u) + 7u)) - 1ull;
                 int t1 = -1, t2 = -1;
-                for (int t = (int)p; t >= 0 && t2 < 0; --t) {
-                    const DigitLoc l = digit_loc((u32)t, key_words);
-                    if ((cm.diff[l.word] >> l.sh) & 0xffu) {
+                for (int t = (int)p; t >= 0 && t2 < 0; --t)
+                    if ((d >> (8 * (t % 8))) & 0xffu) {
                         if (t1 < 0)
                             t1 = t;
                         else
                             t2 = t;
                     }
-                }
-                cm.t1 = t1;
+                cm.t1 = t1 >= 0 ? -3 : -1;  // -3: found without another pass (digits below)
                 cm.t2 = t2;
+                cm.diff[0] = (u64)(t1 < 0 ? 0 : t1);
             }
-            __syncthreads();
+        }
+        __syncthreads();
+        if (cm.t1 < 0) {
+            // the speculation missed: find the bin's two most significant varying
+            // digits (from this pass's OR / AND when p's word is the last key word)
+            if (cm.t1 == -3) {
+                __syncthreads();
+                if (tid == 0)
+                    cm.t1 = (int)cm.diff[0];
+                __syncthreads();
+            } else if (cm.t1 == -2) {
+                // some of digits p, p-1 are constant here: find the bin's two most
+                // significant varying digits from the OR / AND of every key word
+                for (u32 wi = la.word; wi < key_words; ++wi) {
+                    u64 vo = 0, va = ~0ull;
+                    for (u32 i = tid; i < n; i += THREADS) {
+                        const u64 x = __ldcg(src + (u64)i * rw + wi);
+                        vo |= x;
+                        va &= x;
+                    }
+    #pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        vo |= __shfl_xor_sync(FULL_MASK, vo, o);
+                        va &= __shfl_xor_sync(FULL_MASK, va, o);
+                    }
+                    if (lane == 0) {
+                        cm.red_or[0][w] = vo;
+                        cm.red_and[0][w] = va;
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        u64 o2 = 0, a2 = ~0ull;
+                        for (int i = 0; i < NW; ++i) {
+                            o2 |= cm.red_or[0][i];
+                            a2 &= cm.red_and[0][i];
+                        }
+                        u64 d = o2 ^ a2;
+                        if (wi == la.word && p % 8u != 7u)
+                            d &= (2ull << (8u * (p % 8u) + 7u)) - 1ull;  // bytes at or below digit p
+                        cm.diff[wi] = d;
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0) {
+                    int t1 = -1, t2 = -1;
+                    for (int t = (int)p; t >= 0 && t2 < 0; --t) {
+                        const DigitLoc l = digit_loc((u32)t, key_words);
+                        if ((cm.diff[l.word] >> l.sh) & 0xffu) {
+                            if (t1 < 0)
+                                t1 = t;
+                            else
+                                t2 = t;
+                        }
+                    }
+                    cm.t1 = t1;
+                    cm.t2 = t2;
+                }
+                __syncthreads();
+            }
             if (cm.t1 < 0) {
                 // every key of the bin is equal: its order is final
                 if (from_tmp) {
@@ -322,11 +349,21 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
             for (u32 i = tid; i < CODE_WORDS; i += THREADS)
                 cs.cnt[i] = 0;
             __syncthreads();
-            for (u32 i = tid; i < n; i += THREADS) {
-                const u64 wa = __ldcg(src + (u64)i * rw + la.word);
-                const u64 wb = __ldcg(src + (u64)i * rw + lb.word);
-                const u32 c = code_of(wa, wb, la, lb, two);
-                atomicAdd(&cs.cnt[c >> 1], 1u << ((c & 1u) << 4));
+            constexpr u32 U1 = 4;
+            for (u32 i0 = tid; i0 < n; i0 += THREADS * U1) {
+                u64 wa[U1], wb[U1];
+#pragma unroll
+                for (u32 k = 0; k < U1; ++k) {
+                    const u32 i = i0 + k * THREADS;
+                    wa[k] = i < n ? __ldcg(src + (u64)i * rw + la.word) : 0ull;
+                    wb[k] = i < n ? __ldcg(src + (u64)i * rw + lb.word) : 0ull;
+                }
+#pragma unroll
+                for (u32 k = 0; k < U1; ++k)
+                    if (i0 + k * THREADS < n) {
+                        const u32 c = code_of(wa[k], wb[k], la, lb, two);
+                        atomicAdd(&cs.cnt[c >> 1], 1u << ((c & 1u) << 4));
+                    }
             }
             __syncthreads();
         }

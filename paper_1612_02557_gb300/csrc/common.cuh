@@ -98,13 +98,14 @@ struct Caps {
 // Monotone two-level piecewise-linear CDF of key word 0 (the learned first
 // partition).  Level 1 (root): segment j = top byte of the key, with the exact
 // record count R_j of the segment (the first MSD pass's digit histogram) and
-// its exclusive prefix C_j.  Level 2 (leaf, one per segment): the in-segment
-// coordinate t = fp32(key mod 2^56) * 2^-56 goes through two piecewise-linear
-// stages, u = f2(f1(t)).  Each stage has m uniformly spaced knots (stage 1 on
-// the range of the segment's sample, stage 2 on [0, 1]) with learned
-// non-decreasing heights (h_0 = 0, h_{m-1} = 1); a trained stage 1 stretches
-// dense regions of t over their share of [0, 1], so stage 2's uniform knots
-// resolve them.  A key's rank estimate is p = C_j + min(floor(u * R_j), R_j - 1)
+// its exclusive prefix C_j.  Level 2 (leaf, one per segment): the key's low 56
+// bits go through two piecewise-linear stages, u = f2(f1(key)).  Stage 1 has m
+// knots spaced 2^sh apart from the segment's first sample (the smallest power
+// of two that covers the segment's sample range), evaluated in integers: the
+// interval is an exact shift and lam = remainder / 2^sh; stage 2 has m uniform
+// knots on [0, 1].  Heights are learned and non-decreasing (h_0 = 0,
+// h_{m-1} = 1); a trained stage 1 stretches dense key ranges over their share
+// of [0, 1], so stage 2's uniform knots resolve them.  A key's rank estimate is p = C_j + min(floor(u * R_j), R_j - 1)
 // and its bucket b = floor(p * B / n), B = 2^log2B; every step is monotone in
 // the key, so bucket order is key order.  The bucket id is used as two MSD
 // "digits": its top 8 bits and its low (log2B - 8) bits.
@@ -113,28 +114,30 @@ constexpr u32 DIGIT_LEARNED_HI = 0x10000u;  // digit code: top 8 bits of the mod
 constexpr u32 DIGIT_LEARNED_LO = 0x10001u;  // digit code: low bits of the model bucket
 
 struct ModelSeg {
-    float x0;     // first knot
-    float inv_w;  // 1 / knot spacing
+    u64 base;     // stage 1: knot 0 as a 56-bit in-segment key offset
+    float x0;     // stage 2: first knot
+    float inv_w;  // stage 2: 1 / knot spacing
     u32 koff;     // first knot (height) index
     u32 m;        // knots (>= 2)
     u32 poff;     // first parameter index (m - 1 parameters)
-    u32 pad;
+    u32 sh;       // stage 1: knot spacing 2^sh in key units
 };
+static_assert(sizeof(ModelSeg) == 32, "ModelSeg layout");
 
 struct Model {
     ModelSeg seg[2][RADIX];  // stage 1 and stage 2 of every segment's leaf
     u64 root_cnt[RADIX];
     u64 root_c[RADIX];
     const float *h;          // knot heights of both stages (device)
-    const u64 *heavy;        // sorted keys that alone fill >= 4 ideal buckets in the sample
+    const u64 *heavy;        // sorted keys that alone fill >= 1 ideal bucket in the sample
     u64 n;                   // records the model partitions
     u32 log2b;               // log2 of the bucket count (12..16)
     u32 lo_bits;             // log2b - 8
     u32 n_heavy;
-    u32 pad;
+    float inv_n;             // 1 / n (first guess of the bucket division)
 };
 
-constexpr u32 HEAVY_MAX = 2048;  // heavy keys tracked for the balance check
+constexpr u32 HEAVY_MAX = 4096;  // heavy keys tracked for the balance check (the heaviest ones)
 
 // Is `key` one of the model's heavy keys (binary search of a sorted list)?
 __device__ __forceinline__ bool is_heavy(const u64 *list, u32 n, u64 key)
@@ -150,7 +153,50 @@ __device__ __forceinline__ bool is_heavy(const u64 *list, u32 n, u64 key)
     return a < n && list[a] == key;
 }
 
-// One piecewise-linear stage at coordinate x.
+constexpr u64 LOW56 = 0x00FFFFFFFFFFFFFFull;
+
+// 2^-e as a float (0 <= e <= 126), exactly.
+__device__ __forceinline__ float exp2_neg(u32 e) { return __int_as_float((int)(127u - e) << 23); }
+
+// Interpolation of knot interval i of a stage at position lam in [0, 1].
+__device__ __forceinline__ float pl_interp(const ModelSeg &sg, const float *__restrict__ h, u32 i, float lam)
+{
+    const float h0 = h[sg.koff + i], h1 = h[sg.koff + i + 1];
+    return fminf(fmaxf(fmaf(h1 - h0, lam, h0), h0), h1);
+}
+
+// Stage 1 at a key: knots at base + i * 2^sh of the key's low 56 bits.  The
+// interval index is an exact integer shift and lam the exact remainder over
+// the spacing (one rounding), so keys resolve to the last bit at both ends of
+// a segment.  Returns false (and u) when the key is outside the knot range.
+__device__ __forceinline__ bool stage1_coord(const ModelSeg &sg, u64 key, u32 &i, float &lam, float &u)
+{
+    const u64 low = key & LOW56;
+    if (low < sg.base) {
+        u = 0.f;
+        return false;
+    }
+    const u64 off = low - sg.base;
+    const u64 i64 = off >> sg.sh;
+    if (i64 >= (u64)(sg.m - 1u)) {
+        u = 1.f;
+        return false;
+    }
+    i = (u32)i64;
+    lam = (float)(off & ((1ull << sg.sh) - 1ull)) * exp2_neg(sg.sh);
+    return true;
+}
+
+__device__ __forceinline__ float pl_stage1(const ModelSeg &sg, const float *__restrict__ h, u64 key)
+{
+    u32 i = 0;
+    float lam = 0.f, u = 0.f;
+    if (!stage1_coord(sg, key, i, lam, u))
+        return u;
+    return pl_interp(sg, h, i, lam);
+}
+
+// Stage 2 at coordinate x in [0, 1]: uniform knots.
 __device__ __forceinline__ float pl_stage(const ModelSeg &sg, const float *__restrict__ h, float x)
 {
     const float g = (x - sg.x0) * sg.inv_w;
@@ -161,21 +207,30 @@ __device__ __forceinline__ float pl_stage(const ModelSeg &sg, const float *__res
     u32 i = (u32)g;
     if (i > sg.m - 2u)
         i = sg.m - 2u;
-    const float lam = g - (float)i;
-    const float h0 = h[sg.koff + i], h1 = h[sg.koff + i + 1];
-    return fminf(fmaxf(fmaf(h1 - h0, lam, h0), h0), h1);
+    return pl_interp(sg, h, i, g - (float)i);
 }
 
+// Bucket of a key: p = C_j + min(floor(u * R_j), R_j - 1) and b = floor(p * B / n),
+// all in integer arithmetic (u is a float in [0, 1], so u * 2^64 is an exact
+// integer for every u that can make u * R_j reach 1).
 __device__ __forceinline__ u32 model_bucket(const Model *__restrict__ M, u64 key)
 {
     const u32 j = (u32)(key >> 56);
-    const float t = (float)(key & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
-    const float u = pl_stage(M->seg[1][j], M->h, pl_stage(M->seg[0][j], M->h, t));
+    const float u = pl_stage(M->seg[1][j], M->h, pl_stage1(M->seg[0][j], M->h, key));
     const u64 r = M->root_cnt[j];
-    u64 q = (u64)((double)u * (double)r);
+    const u64 uq = u >= 1.f ? ~0ull : __float2ull_rz(u * 0x1p64f);
+    u64 q = __umul64hi(uq, r);
     if (q >= r)
         q = r ? r - 1 : 0;
-    return (u32)(((M->root_c[j] + q) << M->log2b) / M->n);
+    const u64 pb = (M->root_c[j] + q) << M->log2b;
+    const u32 nb = 1u << M->log2b;
+    u32 b = (u32)fminf((float)pb * M->inv_n, (float)(nb - 1u));
+    // the float guess is off by at most a few: settle it exactly
+    while (b > 0 && (u64)b * M->n > pb)
+        --b;
+    while (b + 1u < nb && (u64)(b + 1u) * M->n <= pb)
+        ++b;
+    return b;
 }
 
 // Which digit a pass splits on: a key byte (word, shift) or a model digit.

@@ -442,7 +442,9 @@ cudaError_t model_bufs(ModelBufs &M, u32 S, u32 k_extra)
 
 
 
-constexpr float LEARN_RATE = 0.05f;
+// Adam step size: the warm start already passes through the sample's CDF at
+// every knot, so the steps only refine it (larger steps overshoot).
+constexpr float LEARN_RATE = 0.002f;
 
 // Fit a model of the key words 0 of `in` (n records of rw words) whose exact
 // top-byte histogram is root_hist (device, 256 u64): sample, sort the sample
@@ -474,8 +476,9 @@ int model_fit(Ctx &c, ModelBufs &M, const u64 *in, u64 n, u32 rw, const u64 *roo
                                             M.max_knots, st));
     TIMED(RADULS_K_LEARNED, lm_launch_init(M.theta, M.am, M.av, M.n_params_cap, st));
     {
-        // a key filling >= 4 ideal buckets' worth of the sample is unsplittable
-        const u64 thr = (4ull * S) >> log2b;
+        // a key filling at least an ideal bucket's worth of the sample cannot be
+        // balanced by any bucket map: it is left out of the balance ratio
+        const u64 thr = (u64)S >> log2b;
         TIMED(RADULS_K_LEARNED, lm_launch_heavy(M.sample, S, (u32)(thr > 1 ? thr : 2), M.heavy, M.model, st));
     }
     // stage 1 on its own, then stage 2 on stage 1's output: each warm-started
@@ -861,7 +864,7 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
     j.mode = opts ? opts->mode : 0u;
     j.log2b = opts ? opts->learned_log2_buckets : 0u;
     j.fallback_ratio = opts ? opts->fallback_ratio : 0.f;
-    j.train_steps = (opts && opts->train_steps) ? opts->train_steps : 100u;
+    j.train_steps = (opts && opts->train_steps) ? opts->train_steps : 16u;
     return run_sort(*c, c->main, j, (cudaStream_t)stream);
 }
 

@@ -4,12 +4,13 @@
 //
 // Fit: a strided sample of key words is gathered and sorted (by the sorter
 // itself); per root segment j its first and last sample give the stage-1 knot
-// range, and the knot counts grow with the segment's sample share.  Heights
+// range (knots a power of two apart in key units), and the knot counts grow
+// with the segment's sample share.  Heights
 // are h_i = sum_{l<i} softplus(theta_l) / sum_l softplus(theta_l), initialised
 // uniform (linear stages).  Training minimises the mean squared gap between
 // the leaf's output and the sample's empirical in-segment CDF
-// F_s = (r_s + 0.5) / s_j with Adam, stage 1 on its own first (input t), then
-// stage 2 on f1(t) with stage 1 fixed; forward and backward passes are the
+// F_s = (r_s + 0.5) / s_j with Adam, stage 1 on its own first (input: the
+// key), then stage 2 on f1(key) with stage 1 fixed; forward and backward passes are the
 // kernels below (own derivation of the gradient of one stage with input x:
 //   d u / d theta_l = sigmoid(theta_l) / T_j * ([l < i] + lam [l == i] - u),
 // with i the knot interval of x, lam its position inside the interval and T_j
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__
                                                         u32 *__restrict__ seg_start, u32 max_knots)
 {
     __shared__ u32 s_m[RADIX];
+    __shared__ u32 s_m1[RADIX];
     __shared__ u64 s_c[RADIX];
     const u32 j = threadIdx.x;
     auto lower = [&](u64 key) {  // first sample >= key
@@ -61,7 +63,21 @@ __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__
     u32 m = 2u + (u32)(((u64)k_extra * sj) / (S ? S : 1u));
     if (m > max_knots)
         m = max_knots;
+    // stage 1: knots 2^sh apart from the first sample's low bits, sh the smallest
+    // that covers the segment's sample range with at most m knots
+    u64 base = 0, range = 0;
+    if (sj > 0) {
+        base = sample[st] & LOW56;
+        range = (sample[en - 1] & LOW56) - base;
+    }
+    u32 sh = 0;
+    while (sh < 56u && ((u64)(m - 1u) << sh) <= range)
+        ++sh;
+    u32 m1 = (u32)(range >> sh) + 2u;
+    if (m1 > m)
+        m1 = m;
     s_m[j] = m;
+    s_m1[j] = m1;
     s_c[j] = root_hist[j];
     seg_start[j] = st;
     if (j == RADIX - 1)
@@ -73,7 +89,7 @@ __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__
         for (u32 i = 0; i < RADIX; ++i) {  // stage-1 knots
             M->seg[0][i].koff = off;
             M->seg[0][i].poff = off - i;
-            off += s_m[i];
+            off += s_m1[i];
             M->root_c[i] = c;
             c += s_c[i];
         }
@@ -84,21 +100,20 @@ __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__
         }
         M->h = h_dev;
         M->n = n;
+        M->inv_n = 1.f / (float)n;
         M->log2b = log2b;
         M->lo_bits = log2b - 8u;
     }
     __syncthreads();
     M->root_cnt[j] = s_c[j];
-    float x0 = 0.f, x1 = 1.f;
-    if (sj > 0) {
-        x0 = (float)(sample[st] & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
-        x1 = (float)(sample[en - 1] & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
-    }
-    M->seg[0][j].m = m;
-    M->seg[0][j].x0 = x0;
-    // equal ends (a single distinct value): any larger key is past the last knot
-    M->seg[0][j].inv_w = (x1 > x0) ? (float)(m - 1u) / (x1 - x0) : 1e30f;
+    M->seg[0][j].m = m1;
+    M->seg[0][j].base = base;
+    M->seg[0][j].sh = sh;  // a single distinct value: sh = 0, m1 = 2, larger keys map to 1
+    M->seg[0][j].x0 = 0.f;
+    M->seg[0][j].inv_w = 0.f;
     M->seg[1][j].m = m;
+    M->seg[1][j].base = 0;
+    M->seg[1][j].sh = 0;
     M->seg[1][j].x0 = 0.f;
     M->seg[1][j].inv_w = (float)(m - 1u);
 }
@@ -131,23 +146,22 @@ __global__ void lm_warm_kernel(const Model *__restrict__ M, u32 stage, const u64
         return;
     const ModelSeg sg = M->seg[stage][j];
     const float inv_sj = 1.f / (float)(en - st);
-    auto coord = [&](u32 s) {
-        float x = (float)(sample[s] & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
-        if (stage == 1)
-            x = pl_stage(M->seg[0][j], M->h, x);
-        return x;
-    };
     // fraction of the segment's samples whose input is <= the knot's position
+    // (stage 1: the key's low bits against knot base + i 2^sh; stage 2: the
+    // stage-1 output against the uniform knot)
     auto cdf_at = [&](u32 i) {
         if (i == 0)
             return 0.f;
         if (i + 1 >= sg.m)
             return 1.f;
+        const u64 xk = sg.base + ((u64)i << sg.sh);
         const float xi = sg.x0 + (float)i / sg.inv_w;
-        u32 a = st, b = en;  // first sample with input > xi
+        u32 a = st, b = en;  // first sample with input > the knot
         while (a < b) {
             const u32 mid = (a + b) >> 1;
-            if (coord(mid) <= xi)
+            const bool le = stage == 0 ? (sample[mid] & LOW56) <= xk
+                                       : pl_stage1(M->seg[0][j], M->h, sample[mid]) <= xi;
+            if (le)
                 a = mid + 1;
             else
                 b = mid;
@@ -247,22 +261,30 @@ __global__ void lm_grad_kernel(const Model *__restrict__ M, const u64 *__restric
         u32 ikey = 0xffffffffu;  // global knot index of the interval; none = max
         if (valid) {
             const u32 st = seg_start[j], sj = seg_start[j + 1] - st;
-            float x = (float)(key & 0x00FFFFFFFFFFFFFFull) * 0x1p-56f;
-            if (stage == 1)
-                x = pl_stage(M->seg[0][j], M->h, x);
             const ModelSeg sg = M->seg[stage][j];
-            const float g = (x - sg.x0) * sg.inv_w;
+            // the stage's knot interval i and position lam in it (inside = false:
+            // outside the knot range, u = uo)
+            u32 i = 0;
+            float lam = 0.f, uo = 0.f;
+            bool inside;
+            if (stage == 0) {
+                inside = stage1_coord(sg, key, i, lam, uo);
+            } else {
+                const float g = (pl_stage1(M->seg[0][j], M->h, key) - sg.x0) * sg.inv_w;
+                inside = (g > 0.f) && g < (float)(sg.m - 1u);
+                uo = (g > 0.f) ? 1.f : 0.f;
+                if (inside) {
+                    i = (u32)g;
+                    if (i > sg.m - 2u)
+                        i = sg.m - 2u;
+                    lam = g - (float)i;
+                }
+            }
             const double F = ((double)(s - st) + 0.5) / (double)sj;
             double u;
-            if (!(g > 0.f)) {
-                u = 0.0;
-            } else if (g >= (float)(sg.m - 1u)) {
-                u = 1.0;
+            if (!inside) {
+                u = (double)uo;
             } else {
-                u32 i = (u32)g;
-                if (i > sg.m - 2u)
-                    i = sg.m - 2u;
-                const float lam = g - (float)i;
                 const float h0 = M->h[sg.koff + i], h1 = M->h[sg.koff + i + 1];
                 u = (double)h0 + ((double)h1 - (double)h0) * (double)lam;
                 ikey = sg.koff + i;
@@ -345,26 +367,48 @@ __global__ void lm_update_kernel(const Model *__restrict__ M, u32 stage, float *
 
 // One CTA of 1024 threads: in the sorted sample, every key whose run of equal
 // values is at least thr long (it alone fills that many ideal buckets' worth
-// of the sample) is appended, in key order, to the heavy list (at most
-// HEAVY_MAX keys).
+// of the sample) is appended, in key order, to the heavy list.  When more than
+// HEAVY_MAX keys qualify, thr is doubled until the heaviest fit.
 __global__ void __launch_bounds__(1024) lm_heavy_kernel(const u64 *__restrict__ sample, u32 S, u32 thr,
                                                        u64 *__restrict__ heavy, Model *__restrict__ M)
 {
     __shared__ u32 wcount[32];
     __shared__ u32 base;
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    if (thr < 1)
+        thr = 1;
+    auto is_heavy_start = [&](u32 s, u32 t, u64 &key) {
+        if (s >= S)
+            return false;
+        key = sample[s];
+        const bool start = (s == 0) || sample[s - 1] != key;
+        return start && s + t - 1 < S && sample[s + t - 1] == key;
+    };
+    // pass 1 (repeated): how many keys reach thr; raise thr until they fit
+    for (int round = 0; round < 32; ++round) {
+        if (tid == 0)
+            base = 0;
+        __syncthreads();
+        for (u32 s0 = 0; s0 < S; s0 += 1024) {
+            u64 key = 0;
+            const u32 bal = __ballot_sync(FULL_MASK, is_heavy_start(s0 + tid, thr, key));
+            if (lane == 0 && bal)
+                atomicAdd(&base, (u32)__popc(bal));
+        }
+        __syncthreads();
+        const u32 count = base;
+        __syncthreads();
+        if (count <= HEAVY_MAX || thr >= S)
+            break;
+        thr = thr * 2u;
+    }
+    // pass 2: the list, in key order
     if (tid == 0)
         base = 0;
     __syncthreads();
     for (u32 s0 = 0; s0 < S; s0 += 1024) {
-        const u32 s = s0 + tid;
-        bool hv = false;
         u64 key = 0;
-        if (s < S) {
-            key = sample[s];
-            const bool start = (s == 0) || sample[s - 1] != key;
-            hv = start && thr >= 1 && s + thr - 1 < S && sample[s + thr - 1] == key;
-        }
+        const bool hv = is_heavy_start(s0 + tid, thr, key);
         const u32 bal = __ballot_sync(FULL_MASK, hv);
         if (lane == 0)
             wcount[w] = __popc(bal);

@@ -28,8 +28,8 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
     constexpr int NW = THREADS / 32;
     __shared__ u32 cnt[NW][RADIX + 1];
     __shared__ u32 light[RADIX];         // records per digit whose key is not heavy (model low digit only)
-    __shared__ u64 heavy[HEAVY_MAX];     // the model's heavy keys
     __shared__ u32 s_tile;
+    extern __shared__ u64 heavy[];       // the model's heavy keys (dynamic: HEAVY_MAX words with a model)
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     const u32 n_tiles = ctrs->grid_cur_tiles;
     const u32 n_heavy = model ? model->n_heavy : 0u;
@@ -362,9 +362,16 @@ cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const Wor
         grid = hist_grid(s);
         cached_dev = dev;
     }
-    hist_kernel<HIST_THREADS, HIST_UNROLL><<<grid, HIST_THREADS, 0, st>>>(in, tmp, items, tile_item, hist, orand,
-                                                                         dlight, ctrs, s.tile_h, s.rw, s.key_words,
-                                                                         model);
+    const size_t dyn = model ? (size_t)HEAVY_MAX * 8 : 0;
+    if (model) {
+        const cudaError_t e = cudaFuncSetAttribute(hist_kernel<HIST_THREADS, HIST_UNROLL>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess)
+            return e;
+    }
+    hist_kernel<HIST_THREADS, HIST_UNROLL><<<grid, HIST_THREADS, dyn, st>>>(in, tmp, items, tile_item, hist, orand,
+                                                                           dlight, ctrs, s.tile_h, s.rw, s.key_words,
+                                                                           model);
     return cudaGetLastError();
 }
 

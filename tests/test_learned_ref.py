@@ -156,3 +156,21 @@ def test_gradient_descent_reduces_loss():
         t -= 2.0 * g
     l1, _ = L.loss_and_grad(keys, ko, kx, t)
     assert l1 < 0.5 * l0
+
+
+def test_stage1_coordinate_resolves_the_top_of_a_segment():
+    """Keys a few units apart just below 2^63 (the top of segment 0x7F) get
+    distinct, exactly spaced stage-1 coordinates: the integer offset keeps
+    the last bit, where fp32(key mod 2^56) * 2^-56 would merge 2^32 keys."""
+    seg = np.zeros(256, dtype=[("base", "<u8"), ("sh", "<u4")])
+    seg["base"][0x7F] = (1 << 56) - (1 << 20)
+    seg["sh"][0x7F] = 4
+    keys = np.array([(1 << 63) - 1 - 3 * k for k in range(5)][::-1], dtype=np.uint64)
+    g = L.stage1_coords(keys, seg)
+    assert np.all(np.diff(g) == 3.0 / 16.0)
+    assert g[-1] == ((1 << 20) - 1) / 16.0
+    _, t = L.split_keys(keys)
+    assert np.unique(t).size == 1          # the fp32 coordinate cannot tell them apart
+    below = np.array([(0x7F << 56) | 5], dtype=np.uint64)
+    assert L.stage1_coords(below, seg)[0] == -1.0
+
