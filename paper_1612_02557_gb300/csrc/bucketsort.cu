@@ -81,6 +81,52 @@ __device__ __forceinline__ void discard_range(const void *lo, const void *hi)
         discard_l2_line((const void *)x);
 }
 
+// L2 eviction policies (createpolicy): records read or written for the last
+// time leave L2 first; the private scratch copy stays until it is consumed.
+__device__ __forceinline__ u64 l2_evict_first()
+{
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ u64 l2_evict_last()
+{
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+template <int RW>
+__device__ __forceinline__ void load_rec_hint(u64 (&r)[RW], const u64 *g, u64 pol)
+{
+#pragma unroll
+    for (int i = 0; i < RW; i += 2) {
+        if (i + 1 < RW) {
+            asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                         : "=l"(r[i]), "=l"(r[i + 1])
+                         : "l"(g + i), "l"(pol));
+        } else {
+            asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r[i]) : "l"(g + i), "l"(pol));
+        }
+    }
+}
+
+template <int RW>
+__device__ __forceinline__ void store_rec_hint(u64 *g, const u64 (&r)[RW], u64 pol)
+{
+#pragma unroll
+    for (int i = 0; i < RW; i += 2) {
+        if (i + 1 < RW) {
+            asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(g + i), "l"(r[i]),
+                         "l"(r[i + 1]), "l"(pol)
+                         : "memory");
+        } else {
+            asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(g + i), "l"(r[i]), "l"(pol) : "memory");
+        }
+    }
+}
+
 // Word w of a record held in registers (unrolled select: no local memory).
 template <int RW>
 __device__ __forceinline__ u64 rec_word(const u64 (&r)[RW], u32 w)
@@ -411,6 +457,7 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
         if (mx <= GROUP_MAX) {
             // this CTA's private scratch region (reused bin after bin, so it stays in L2)
             u64 *const scr = a.bucket_scratch + (u64)blockIdx.x * a.bucket_max * rw;
+            const u64 pol_first = l2_evict_first(), pol_last = l2_evict_last();
             // ---- 3. placement by code (group starts -> running ends), original index kept
             u32 run = sum;
             for (u32 j = 0; j < CW; ++j) {
@@ -427,7 +474,7 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
                 for (u32 k = 0; k < U; ++k) {
                     const u32 i = i0 + k * THREADS;
                     if (i < n)
-                        load_rec<RW>(r[k], src + (u64)i * rw);
+                        load_rec_hint<RW>(r[k], src + (u64)i * rw, pol_first);
                 }
 #pragma unroll
                 for (u32 k = 0; k < U; ++k) {
@@ -437,7 +484,7 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
                         const u32 sh = (c & 1u) << 4;
                         const u32 pos = (atomicAdd(&cs.cnt[c >> 1], 1u << sh) >> sh) & 0xffffu;
                         if (pos < n) {
-                            store_rec<RW>(scr + (u64)pos * rw, r[k]);
+                            store_rec_hint<RW>(scr + (u64)pos * rw, r[k], pol_last);
                             cs.oidx[pos] = (unsigned short)i;
                         } else {
                             set_error(a.ctrs, ST_INTERNAL);
@@ -459,7 +506,7 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
 #pragma unroll
                 for (u32 k = 0; k < U4; ++k)
                     if (q0 + k * THREADS < n)
-                        load_rec<RW>(rr[k], scr + (u64)(q0 + k * THREADS) * rw);
+                        load_rec_hint<RW>(rr[k], scr + (u64)(q0 + k * THREADS) * rw, pol_first);
 #pragma unroll
                 for (u32 k = 0; k < U4; ++k) {
                     const u32 q = q0 + k * THREADS;
@@ -501,7 +548,7 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
                                 ++rank;
                     }
                     if (valid)
-                        store_rec<RW>(out + (u64)(g > 1 ? s + rank : q) * rw, rr[k]);
+                        store_rec_hint<RW>(out + (u64)(g > 1 ? s + rank : q) * rw, rr[k], pol_first);
                 }
             }
             __syncthreads();

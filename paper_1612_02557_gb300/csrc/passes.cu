@@ -28,6 +28,7 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
     constexpr int NW = THREADS / 32;
     __shared__ u32 cnt[NW][RADIX + 1];
     __shared__ u32 light[RADIX];         // records per digit whose key is not heavy (model low digit only)
+    __shared__ u64 red_or[NW], red_and[NW];
     __shared__ u32 s_tile;
     extern __shared__ u64 heavy[];       // the model's heavy keys (dynamic: HEAVY_MAX words with a model)
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
@@ -35,23 +36,72 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
     const u32 n_heavy = model ? model->n_heavy : 0u;
     for (u32 i = tid; i < n_heavy; i += THREADS)
         heavy[i] = model->heavy[i];
+    for (u32 i = lane; i < RADIX + 1; i += 32)
+        cnt[w][i] = 0;
+    if (tid < RADIX)
+        light[tid] = 0;
+    // Counts, OR / AND and bytes accumulate over consecutive tiles of the same
+    // bin and go to global memory when the bin changes (or at the end): the
+    // tiles of one big bin would otherwise all hit the same few counters.
+    u32 cur_row = ~0u, cur_learned = 0;
+    u64 vor = 0, vand = ~0ull, bytes = 0;
     for (;;) {
         if (tid == 0)
             s_tile = atomicAdd(&ctrs->tile_ctr[0], 1u);
-        for (u32 i = lane; i < RADIX + 1; i += 32)
-            cnt[w][i] = 0;
-        if (tid < RADIX)
-            light[tid] = 0;
         __syncthreads();
         const u32 t = s_tile;
+        const u32 next_row = t < n_tiles ? items[tile_item[t]].row : ~0u;
+        if (next_row != cur_row && cur_row != ~0u) {
+            if (tid < RADIX) {
+                u32 s = 0;
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww)
+                    s += cnt[ww][tid];
+                if (s)
+                    atomicAdd(&hist[(u64)cur_row * RADIX + tid], (u64)s);
+                if (cur_learned == 2 && light[tid])
+                    atomicAdd(&dlight[(u64)cur_row * RADIX + tid], (u64)light[tid]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vor |= __shfl_xor_sync(FULL_MASK, vor, o);
+                vand &= __shfl_xor_sync(FULL_MASK, vand, o);
+            }
+            if (lane == 0) {
+                red_or[w] = vor;
+                red_and[w] = vand;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                u64 o2 = 0, a2 = ~0ull;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    o2 |= red_or[i];
+                    a2 &= red_and[i];
+                }
+                atomicOr(&orand[2ull * cur_row], o2);
+                atomicAnd(&orand[2ull * cur_row + 1], a2);
+                atomicAdd(&ctrs->hist_bytes, bytes);
+            }
+            for (u32 i = lane; i < RADIX + 1; i += 32)
+                cnt[w][i] = 0;
+            if (tid < RADIX)
+                light[tid] = 0;
+            vor = 0;
+            vand = ~0ull;
+            bytes = 0;
+            __syncthreads();
+        }
         if (t >= n_tiles)
             break;
         const WorkItem item = items[tile_item[t]];
+        cur_row = item.row;
         const u64 lo = item.begin + (u64)(t - item.tile_base) * tile_recs;
         const u64 hi = min(item.begin + item.count, lo + tile_recs);
         const u64 *src = (item.flags & ITEM_IN_TMP) ? tmp : in;
         const DigitSel sel = digit_sel(item.digit, key_words);
-        u64 vor = 0, vand = ~0ull;
+        cur_learned = sel.learned;
+        bytes += (hi - lo) * (u64)min(rw * 8u, 32u);
         for (u64 base = lo; base < hi; base += (u64)THREADS * UNROLL) {
             u64 key[UNROLL];
 #pragma unroll
@@ -80,29 +130,6 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
                 }
             }
         }
-        __syncthreads();
-        if (tid < RADIX) {
-            u32 s = 0;
-#pragma unroll
-            for (int ww = 0; ww < NW; ++ww)
-                s += cnt[ww][tid];
-            if (s) {
-                atomicAdd(&hist[(u64)item.row * RADIX + tid], (u64)s);
-                if (sel.learned == 2 && light[tid])
-                    atomicAdd(&dlight[(u64)item.row * RADIX + tid], (u64)light[tid]);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vor |= __shfl_xor_sync(FULL_MASK, vor, o);
-            vand &= __shfl_xor_sync(FULL_MASK, vand, o);
-        }
-        if (lane == 0) {
-            atomicOr(&orand[2ull * item.row], vor);
-            atomicAnd(&orand[2ull * item.row + 1], vand);
-        }
-        if (tid == 0)
-            atomicAdd(&ctrs->hist_bytes, (hi - lo) * (u64)min(rw * 8u, 32u));
         __syncthreads();
     }
 }
