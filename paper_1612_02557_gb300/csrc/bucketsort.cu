@@ -542,10 +542,27 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
                         }
                     }
                     if (valid && g > 1 && !inwin) {
-                        for (u32 j = 0; j < g; ++j)
-                            if (s + j != q && rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, cs.oidx[s + j], oq,
-                                                       w0, key_words))
-                                ++rank;
+                        // a group across two windows: its members' first compared key
+                        // words come in one batch of loads (one round trip)
+                        for (u32 j0 = 0; j0 < g; j0 += 4) {
+                            u64 km[4];
+#pragma unroll
+                            for (u32 jj = 0; jj < 4; ++jj)
+                                km[jj] = j0 + jj < g ? __ldcg(scr + (u64)(s + j0 + jj) * rw + w0) : 0ull;
+#pragma unroll
+                            for (u32 jj = 0; jj < 4; ++jj) {
+                                const u32 j = j0 + jj;
+                                if (j < g && s + j != q) {
+                                    bool lt;
+                                    if (km[jj] != kq)
+                                        lt = km[jj] < kq;
+                                    else
+                                        lt = rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, cs.oidx[s + j], oq,
+                                                      w0 + 1, key_words);
+                                    rank += lt ? 1u : 0u;
+                                }
+                            }
+                        }
                     }
                     if (valid)
                         store_rec_hint<RW>(out + (u64)(g > 1 ? s + rank : q) * rw, rr[k], pol_first);
