@@ -65,6 +65,10 @@ struct Counters {
     u32 bucket_next;      // mid-size bins found in this level
     u32 bucket_split;     // mid-size bins of this level left to the stable split
     u32 split_ctr;        // dynamic item counter of the stable split
+    u32 bmid;             // batched: arrays of the mid-size class (persistent kernel's queue)
+    u32 q_head;           // batched persistent kernel: next queue slot to take
+    u32 q_tail;           // batched persistent kernel: next slot for a pushed item
+    u32 in_flight;        // batched persistent kernel: items queued or in work, not finished
     u32 err;              // first device-detected error (ST_*)
     u32 grid_passes;      // distribution passes run
     u64 skipped;          // constant digits skipped

@@ -83,6 +83,7 @@ struct Work {
     u32 *epoch = nullptr;        // device: look-back epoch of the last distribution launch, wrap flag
     DevBuf lists, hist, status, tiles;
     DevBuf bscratch;  // private scratch regions of the mid-size bin kernel's CTAs
+    DevBuf bqueue;    // batched persistent kernel: mid-size array list, pushed items, ready flags
 };
 
 // Device buffers of one learned model (see the Model struct in common.cuh).
@@ -689,17 +690,17 @@ struct BatchGraph {
     const void *off = nullptr;
     u64 n = 0;
     u32 n_segs = 0, rw = 0, kw = 0;
-    void *ws[5] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
+    void *ws[6] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
 };
 
 BatchGraph g_batch[MAX_DEVICES];
 
 int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, u64 n, u32 rw,
-                    u32 kw, Lists &L, LevelBufs &B, cudaStream_t st)
+                    u32 kw, Lists &L, LevelBufs &B, const BatchQueue &q, cudaStream_t st)
 {
     const u32 top = 8u * kw - 1u;
     CK(launch_batched_init(off, n_segs, L.grid[0], L.blocks, L.tile_hist, wk.ctrs, L.caps, top, s.cap_b, s.tile_h,
-                           L.bkt[0], s.bucket_max, st));
+                           const_cast<WorkItem *>(q.mid), s.bucket_max, st));
     int cur = 0;
     const u32 levels = 8u * kw;
     for (u32 level = 0; level < levels; ++level) {
@@ -743,7 +744,23 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
     }
     CK(launch_check_drained(wk.ctrs, st));
     CK(launch_copy(s, in, tmp, L.copies, L.tile_copy, wk.ctrs, st));
-    CK(launch_block_sort(s, in, tmp, L.blocks, wk.ctrs, off, st));
+    if (s.bucket_var >= 0) {
+        // one persistent launch: mid-size arrays, then every on-chip item
+        PlanArgs a{};
+        a.ctrs = wk.ctrs;
+        a.caps = L.caps;
+        a.key_words = kw;
+        a.rw = rw;
+        a.cap_b = s.cap_b;
+        a.warp_bin = WARP_BIN;
+        a.tile_h = s.tile_h;
+        a.top_digit = top;
+        a.bucket_max = s.bucket_max;
+        a.bucket_scratch = (u64 *)wk.bscratch.p;
+        CK(launch_batched_persistent(s, in, tmp, a, q, off, c.wait_ns, st));
+    } else {
+        CK(launch_block_sort(s, in, tmp, L.blocks, wk.ctrs, off, st));
+    }
     fold_status_kernel<<<1, 1, 0, st>>>(wk.ctrs, c.dev_status);
     CK(cudaGetLastError());
     return RADULS_OK;
@@ -761,14 +778,31 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
     CK(work_level(wk, s, n, L.caps.grid, B, L.caps, st));
     if (s.bucket_max)
         CK(ensure(wk.bscratch, (size_t)bucket_grid() * s.bucket_max * rw * 8, false));
+    // the persistent kernel's queue: mid-size arrays (<= n_segs), pushed items
+    // (each a sub-bin of more than one on-chip group), ready flags
+    BatchQueue q{};
+    {
+        const u64 cap_dyn = n / 4096 + 64;
+        const size_t o_mid = 0, o_dyn = align256((size_t)(n_segs + 1) * sizeof(WorkItem)),
+                     o_rdy = o_dyn + align256((size_t)cap_dyn * sizeof(WorkItem)), total = o_rdy + cap_dyn * 4;
+        if (cap_dyn > 0xffffffffull)
+            return RADULS_ERR_UNSUPPORTED;
+        CK(ensure(wk.bqueue, total, false));
+        char *b = (char *)wk.bqueue.p;
+        q.mid = (const WorkItem *)(b + o_mid);
+        q.blocks = L.blocks;
+        q.dyn = (WorkItem *)(b + o_dyn);
+        q.ready = (u32 *)(b + o_rdy);
+        q.cap_dyn = (u32)cap_dyn;
+    }
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
         c.wait_ns = g_wait_ns;
     }
     BatchGraph &bg = g_batch[dev];
-    void *const ws[5] = {wk.lists.p, wk.hist.p, wk.status.p, wk.tiles.p, wk.bscratch.p};
+    void *const ws[6] = {wk.lists.p, wk.hist.p, wk.status.p, wk.tiles.p, wk.bscratch.p, wk.bqueue.p};
     bool same_ws = true;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
         same_ws = same_ws && bg.ws[i] == ws[i];
     const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
                      bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws;
@@ -785,7 +819,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
             CK(cudaStreamCreateWithFlags(&bg.cap, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(bg.cap, cudaStreamCaptureModeRelaxed));
-        int rc = enqueue_batched(c, wk, s, in, tmp, off, n_segs, n, rw, kw, L, B, bg.cap);
+        int rc = enqueue_batched(c, wk, s, in, tmp, off, n_segs, n, rw, kw, L, B, q, bg.cap);
         cudaError_t e = cudaStreamEndCapture(bg.cap, &graph);
         if (rc)
             return rc;
@@ -800,7 +834,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         bg.n_segs = n_segs;
         bg.rw = rw;
         bg.kw = kw;
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 6; ++i)
             bg.ws[i] = ws[i];
     }
     CK(cudaGraphLaunch(bg.exec, st));

@@ -119,6 +119,20 @@ __device__ __forceinline__ void append_bin(const PlanArgs &a, u64 begin, u64 cou
 // CTA that reads it from HBM once and keeps its scratch copy in L2.
 cudaError_t launch_bucket(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, cudaStream_t st);
 
+// Device queue of the batched persistent kernel: the mid-size arrays first
+// (largest work), then the on-chip items (blocks list), then items the kernel
+// pushes itself (slots published through ready[]).
+struct BatchQueue {
+    const WorkItem *mid;
+    const WorkItem *blocks;
+    WorkItem *dyn;
+    u32 *ready;
+    u32 cap_dyn;
+};
+
+cudaError_t launch_batched_persistent(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, const BatchQueue &q,
+                                      const u64 *seg_off, u64 wait_ns, cudaStream_t st);
+
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
                         u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, cudaStream_t st);
 cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint,

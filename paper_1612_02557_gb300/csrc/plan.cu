@@ -320,8 +320,9 @@ __global__ void batched_validate_kernel(const u64 *__restrict__ off, u32 n_segs,
             set_error(ctrs, ST_BAD_ARG);
 }
 
-// Classify every array by size: bigger than cap_b -> first grid list (its top
-// key digit); bigger than warp_bin -> one on-chip item; otherwise -> a run of
+// Classify every array by size: bigger than a mid-size bin -> first grid list
+// (its top key digit); bigger than cap_b -> the persistent kernel's mid-size
+// queue; bigger than warp_bin -> one on-chip item; otherwise -> a run of
 // consecutive small arrays whose starts share a window of `win` records and
 // whose indices share a block of 256 (so a run holds < cap_b records and at
 // most 256 arrays), sorted one warp per array.
@@ -336,8 +337,9 @@ __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs,
     for (u32 s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x) {
         const u64 a = off[s], c = off[s + 1] - a;
         if (c > cap_b && c <= bucket_max) {
-            const u32 slot = atomicAdd(&ctrs->bucket_cur, 1u);
-            if (slot >= caps.grid) {
+            // mid-size arrays: the persistent kernel's queue (largest work first)
+            const u32 slot = atomicAdd(&ctrs->bmid, 1u);
+            if (slot >= n_segs) {
                 set_error(ctrs, ST_INTERNAL);
                 continue;
             }

@@ -86,3 +86,26 @@ def test_bad_offsets_are_reported_and_nothing_moves():
     p.raduls_sort_batched(d, t, d_off, 3, 16, 8)
     assert p.raduls_stream_status() == 1
     np.testing.assert_array_equal(from_dev(d, 1000, 2), recs)
+
+
+def test_pushed_sub_bins_and_heavy_groups(oracle_mod):
+    """Mid-size arrays whose two top varying digits leave groups too large for
+    code ranks take the stable split; their sub-bins bigger than one on-chip
+    group are pushed back to the persistent kernel's queue and sorted by
+    whichever CTA takes them."""
+    rng = np.random.default_rng(21)
+    sizes = np.array([30000, 500, 25000, 4097, 12, 30001, 40960, 100, 20000], dtype=np.int64)
+    recs, offs = datagen.batched16(sizes=sizes)
+    k = recs[:, 0].copy()
+    for a in range(sizes.size):
+        lo, hi = int(offs[a]), int(offs[a + 1])
+        if hi - lo < 10000:
+            continue
+        m = hi - lo
+        low = rng.integers(0, 1 << 48, size=m, dtype=np.uint64)
+        byte6 = np.where(rng.random(m) < 0.6, 0, rng.integers(1, 256, size=m)).astype(np.uint64)
+        k[lo:hi] = (np.uint64(0x11) << np.uint64(56)) | (byte6 << np.uint64(48)) | low
+        if a % 2:  # a few exact duplicates as well
+            k[lo:lo + 3000] = k[lo]
+    recs[:, 0] = k
+    _check(oracle_mod, recs, offs, 8, repeat=2)
