@@ -263,6 +263,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip raduls_autotune before the warm-up")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -315,6 +316,16 @@ def main():
             pkg.raduls_sort_batched(recs, tmp, d_off, offsets.size - 1, rec, key)
             return None
         return pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode=how, stats=stats)
+
+    # launch shapes and size-class thresholds tuned on seeded records of the
+    # same size and layout (untimed; recs and tmp serve as its scratch)
+    tuning = None
+    if not args.no_tune:
+        if mode == "batched":
+            tuning = pkg.raduls_autotune(recs, tmp, n, rec, key, d_off, offsets.size - 1)
+        else:
+            tuning = pkg.raduls_autotune(recs, tmp, n, rec, key)
+        torch.cuda.synchronize()
 
     # warm-up (untimed), first one checked
     for i in range(args.warmup):
@@ -476,7 +487,8 @@ def main():
         "config": {"workload": args.workload, "desc": w["desc"], "n_records": n, "rec_bytes": rec,
                    "key_bytes": key, "mode": mode,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "input 32 GiB-class, far larger than L2; restored from a pristine device copy before each step"},
+                   "l2": "input 32 GiB-class, far larger than L2; restored from a pristine device copy before each step",
+                   "tuning": tuning},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

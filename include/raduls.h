@@ -214,6 +214,35 @@ int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_
 int raduls_histogram_static(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                             uint32_t digit, uint64_t *d_hist_out, void *stream);
 
+/* Settings picked by raduls_autotune. */
+typedef struct {
+    int32_t  scatter_variant;  /* distribution kernel shape (threads x records per thread) */
+    uint32_t scatter_tile;     /* records per distribution tile of that shape */
+    uint32_t block_cap;        /* largest bin (or run of small bins / arrays) sorted by one CTA on chip */
+    uint32_t bucket_max;       /* largest mid-size bin sorted by one CTA through L2 (0: class off) */
+    float    best_ms;          /* sort time of the chosen setting on the tuning input */
+    uint32_t candidates;       /* settings timed */
+} raduls_tuning;
+
+/* Autotuner of the launch shapes and size-class thresholds (the paper has no
+ * counterpart; its scheduling constants, Sec. 3.2-3.5, are CPU-specific).
+ * Fills `in` with seeded uniform records (SplitMix64 words), sorts them once
+ * per candidate setting -- every distribution tile shape that fits the
+ * record width, the on-chip class at its full and half capacity, the
+ * mid-size class off, at half and at full size -- with `tmp` as scratch,
+ * times each with CUDA events (best of two), and keeps the fastest for later
+ * calls on this device with this record width: plain sorts when
+ * d_seg_offsets is NULL, batched sorts (with those offsets) otherwise.  The
+ * digit width stays 8 bits.  `in` and `tmp` hold n_recs records; their
+ * contents are undefined afterwards.  Synchronises `stream`; not for use
+ * inside a stream capture.  `out` may be NULL.  Environment overrides
+ * (RADULS_SCATTER_VARIANT, RADULS_BUCKET_MAX) still take precedence. */
+int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                    const uint64_t *d_seg_offsets, uint32_t n_segs, raduls_tuning *out, void *stream);
+
+/* Forget every tuned setting (back to the built-in shapes). */
+int raduls_autotune_reset(void);
+
 /* Test hook: make the next distribution pass withhold tile `tile`'s published
  * counts so that its successors' bounded waits run out (kind 1), or clear the
  * hook (kind 0).  The pass then reports RADULS_ERR_TIMEOUT through

@@ -104,6 +104,8 @@ def load():
             "raduls_sort": [vp, vp, u64, u32, u32, vp],
             "raduls_sort_ex": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_sort_batched": [vp, vp, vp, u32, u32, u32, vp],
+            "raduls_autotune": [vp, vp, u64, u32, u32, vp, u32, vp, vp],
+            "raduls_autotune_reset": [],
             "raduls_histogram": [vp, u64, u32, u32, u32, vp, vp],
             "raduls_histogram_static": [vp, u64, u32, u32, u32, vp, vp],
             "raduls_distribution_pass": [vp, vp, u64, u32, u32, u32, vp],
@@ -200,6 +202,38 @@ def raduls_sort_batched(in_, tmp, seg_offsets, n_segs: int, rec_bytes: int, key_
     rc = load().raduls_sort_batched(_addr(in_), _addr(tmp), _addr(seg_offsets), n_segs, rec_bytes, key_bytes,
                                     _stream(stream, in_, tmp))
     _raise(rc, "raduls_sort_batched")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("scatter_variant", ctypes.c_int32),
+        ("scatter_tile", ctypes.c_uint32),
+        ("block_cap", ctypes.c_uint32),
+        ("bucket_max", ctypes.c_uint32),
+        ("best_ms", ctypes.c_float),
+        ("candidates", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def raduls_autotune(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, seg_offsets=None, n_segs: int = 0,
+                    stream=None) -> dict:
+    """Tune launch shapes and size-class thresholds on seeded records written
+    into in_ (in_ and tmp are scratch); returns the chosen settings."""
+    _check_size(in_, n_recs * rec_bytes, "in")
+    _check_size(tmp, n_recs * rec_bytes, "tmp")
+    t = Tuning()
+    rc = load().raduls_autotune(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes,
+                                _addr(seg_offsets) if seg_offsets is not None else None, n_segs,
+                                ctypes.byref(t), _stream(stream, in_, tmp))
+    _raise(rc, "raduls_autotune")
+    return t.as_dict()
+
+
+def raduls_autotune_reset() -> None:
+    _raise(load().raduls_autotune_reset(), "raduls_autotune_reset")
 
 
 def raduls_histogram(in_, n_recs: int, rec_bytes: int, key_bytes: int, digit: int, hist_out, stream=None) -> None:

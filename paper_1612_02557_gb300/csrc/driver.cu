@@ -20,7 +20,46 @@ namespace raduls {
 u32 scatter_tile_of(int var);
 u32 block_cap_of(int var);
 
-Shape choose_shape(u32 rw, u32 key_words)
+// Distribution variants that fit a record width (see SCATTER_VARIANTS).
+bool scatter_variant_fits(int v, u32 rw)
+{
+    switch (v) {
+    case 0:
+        return rw == 1;
+    case 1:
+    case 5:
+    case 6:
+    case 7:
+        return rw == 2;
+    case 2:
+        return rw == 4;
+    case 3:
+        return rw <= 8;
+    case 4:
+        return true;
+    default:
+        return false;
+    }
+}
+
+namespace {
+
+// Settings picked by raduls_autotune, per device, record width and call kind
+// (plain, batched); `force` is the candidate being timed by the tuner itself.
+struct Tuned {
+    bool valid = false;
+    int scat_var = 0;
+    u32 cap_b = 0;
+    u32 bucket_max = 0;
+};
+constexpr int TUNE_DEVICES = 64;
+Tuned g_tuned[TUNE_DEVICES][2][33];
+std::mutex g_tuned_mu;
+thread_local const Tuned *g_force = nullptr;
+
+}  // namespace
+
+Shape choose_shape(u32 rw, u32 key_words, bool batched)
 {
     Shape s{};
     s.rw = rw;
@@ -43,22 +82,40 @@ Shape choose_shape(u32 rw, u32 key_words)
         s.scat_var = 4;
         s.block_var = 4;
     }
-    if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
-        const int want = atoi(v);
-        const bool fits = (want == 10 && rw == 1) || ((want == 11 || want == 13 || want == 14) && rw == 2) ||
-                          ((want == 12 || want == 15) && rw == 4) || (want == 0 && rw == 1) ||
-                          ((want == 1 || want == 5 || want == 6 || want == 7) && rw == 2) || (want == 2 && rw == 4);
-        if (fits)
-            s.scat_var = want;
-    }
-    s.tile_s = scatter_tile_of(s.scat_var);
     s.cap_b = block_cap_of(s.block_var);
-    // mid-size bins: one CTA splits a bin of up to BUCKET_BYTES through L2
+    // mid-size bins: one CTA sorts a bin of up to BUCKET_BYTES through L2
     constexpr u32 BUCKET_BYTES = 640u * 1024u;
     s.bucket_var = rw == 1 ? 0 : rw == 2 ? 1 : rw == 4 ? 2 : -1;
     s.bucket_max = s.bucket_var < 0 ? 0u : BUCKET_BYTES / (rw * 8u);
+    // tuned settings (raduls_autotune), else the defaults above
+    Tuned t{};
+    if (g_force) {
+        t = *g_force;
+    } else {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < TUNE_DEVICES && rw <= 32) {
+            std::lock_guard<std::mutex> g(g_tuned_mu);
+            t = g_tuned[dev][batched ? 1 : 0][rw];
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (t.valid) {
+        if (scatter_variant_fits(t.scat_var, rw))
+            s.scat_var = t.scat_var;
+        if (t.cap_b > WARP_BIN && t.cap_b <= s.cap_b)
+            s.cap_b = t.cap_b;
+        if (s.bucket_var >= 0)
+            s.bucket_max = t.bucket_max;
+    }
+    if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
+        const int want = atoi(v);
+        if (scatter_variant_fits(want, rw))
+            s.scat_var = want;
+    }
     if (const char *v = getenv("RADULS_BUCKET_MAX"))
         s.bucket_max = s.bucket_var < 0 ? 0u : (u32)strtoul(v, nullptr, 10);
+    s.tile_s = scatter_tile_of(s.scat_var);
     if (s.bucket_max > BUCKET_IDX_MAX)  // positions inside a mid-size bin are 16-bit
         s.bucket_max = BUCKET_IDX_MAX;
     if (s.bucket_max <= s.cap_b)
@@ -690,6 +747,8 @@ struct BatchGraph {
     const void *off = nullptr;
     u64 n = 0;
     u32 n_segs = 0, rw = 0, kw = 0;
+    int scat_var = -1;
+    u32 cap_b = 0, bucket_max = 0;  // the shape the graph was captured with
     void *ws[6] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
 };
 
@@ -770,7 +829,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
                 cudaStream_t st)
 {
     Work &wk = c.main;
-    const Shape s = choose_shape(rw, kw);
+    const Shape s = choose_shape(rw, kw, true);
     Lists L{};
     // the batched init adds up to n_segs on-chip items and (n / cap_b) runs to the usual bounds
     CK(work_lists(wk, s, n + 2ull * n_segs + 2ull * s.cap_b, L));
@@ -805,7 +864,8 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
     for (int i = 0; i < 6; ++i)
         same_ws = same_ws && bg.ws[i] == ws[i];
     const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
-                     bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws;
+                     bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws && bg.scat_var == s.scat_var &&
+                     bg.cap_b == s.cap_b && bg.bucket_max == s.bucket_max;
     if (!hit) {
         if (bg.exec) {
             cudaGraphExecDestroy(bg.exec);
@@ -836,6 +896,9 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         bg.kw = kw;
         for (int i = 0; i < 6; ++i)
             bg.ws[i] = ws[i];
+        bg.scat_var = s.scat_var;
+        bg.cap_b = s.cap_b;
+        bg.bucket_max = s.bucket_max;
     }
     CK(cudaGraphLaunch(bg.exec, st));
     return RADULS_OK;
@@ -851,6 +914,24 @@ Ctx *current_ctx(int *status)
     }
     *status = RADULS_OK;
     return &g_ctx[dev];
+}
+
+}  // namespace
+}  // namespace raduls
+
+namespace raduls {
+namespace {
+
+// Tuning input: word i of the buffer is the SplitMix64 output for counter
+// seed + i (Steele, Lea, Flood 2014): uniform keys and payloads.
+__global__ void tune_fill_kernel(u64 *__restrict__ out, u64 words, u64 seed)
+{
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (u64)gridDim.x * blockDim.x) {
+        u64 z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        out[i] = z ^ (z >> 31);
+    }
 }
 
 }  // namespace
@@ -1097,6 +1178,142 @@ int raduls_sort_batched(void *in, void *tmp, const uint64_t *d_seg_offsets, uint
         return to_status(e);
     return run_batched(*c, dev, (u64 *)in, (u64 *)tmp, (const u64 *)d_seg_offsets, n_segs, n, rec_bytes / 8u,
                        key_bytes / 8u, st);
+}
+
+int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                    const uint64_t *d_seg_offsets, uint32_t n_segs, raduls_tuning *out, void *stream)
+{
+    int rc = check_args(in, tmp, n_recs, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n_recs < 2 || (d_seg_offsets && n_segs == 0))
+        return RADULS_ERR_INVALID_ARG;
+    if (d_seg_offsets && ((uintptr_t)d_seg_offsets & 7u))
+        return RADULS_ERR_MISALIGNED;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= TUNE_DEVICES || rec_bytes / 8u > 32u)
+        return RADULS_ERR_UNSUPPORTED;
+    const bool batched = d_seg_offsets != nullptr;
+    const u32 rw = rec_bytes / 8u, kw = key_bytes / 8u;
+    cudaStream_t st = (cudaStream_t)stream;
+    // candidates: every distribution variant of this record width, the on-chip
+    // class at its full and half size, the mid-size class off / half / full
+    Tuned none{};
+    g_force = &none;
+    const Shape base = choose_shape(rw, kw, batched);
+    g_force = nullptr;
+    int vars[8];
+    int nv = 0;
+    for (int v = 0; v < 8; ++v)
+        if (scatter_variant_fits(v, rw) && !(v >= 3 && rw <= 4 && v != base.scat_var))
+            vars[nv++] = v;
+    const u32 caps[2] = {base.cap_b, base.cap_b / 2};
+    const u32 bmaxes[3] = {0u, base.bucket_max / 2, base.bucket_max};
+    const int nb = base.bucket_max ? 3 : 1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return RADULS_ERR_CUDA;
+    }
+    Tuned best{};
+    float best_ms = 0.f;
+    u32 timed = 0;
+    rc = RADULS_OK;
+    for (int vi = 0; vi < nv && rc == RADULS_OK; ++vi)
+        for (int ci = 0; ci < 2 && rc == RADULS_OK; ++ci)
+            for (int bi = 0; bi < nb && rc == RADULS_OK; ++bi) {
+                Tuned t{};
+                t.valid = true;
+                t.scat_var = vars[vi];
+                t.cap_b = caps[ci];
+                t.bucket_max = bmaxes[bi] > caps[ci] ? bmaxes[bi] : 0u;
+                if (bi > 0 && t.bucket_max == 0)
+                    continue;
+                float ms_min = 0.f;
+                for (int rep = 0; rep < 2 && rc == RADULS_OK; ++rep) {
+                    tune_fill_kernel<<<1024, 256, 0, st>>>((u64 *)in, n_recs * rw, 0x5241445553ull + rep);
+                    if (cudaGetLastError() != cudaSuccess) {
+                        rc = RADULS_ERR_CUDA;
+                        break;
+                    }
+                    g_force = &t;
+                    cudaEventRecord(e0, st);
+                    {
+                        std::lock_guard<std::mutex> g(c->mu);
+                        cudaError_t e = ctx_init(*c);
+                        if (e != cudaSuccess) {
+                            rc = to_status(e);
+                        } else if (batched) {
+                            rc = run_batched(*c, dev, (u64 *)in, (u64 *)tmp, (const u64 *)d_seg_offsets, n_segs,
+                                             n_recs, rw, kw, st);
+                        } else {
+                            SortJob j{};
+                            j.in = (u64 *)in;
+                            j.tmp = (u64 *)tmp;
+                            j.n = n_recs;
+                            j.rw = rw;
+                            j.kw = kw;
+                            j.mode = 1;
+                            j.train_steps = 16u;
+                            rc = run_sort(*c, c->main, j, st);
+                        }
+                    }
+                    g_force = nullptr;
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaGetLastError();
+                        rc = RADULS_ERR_CUDA;
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms_min = (rep == 0 || ms < ms_min) ? ms : ms_min;
+                }
+                if (rc == RADULS_OK) {
+                    const int srt = raduls_stream_status(stream);
+                    if (srt != RADULS_OK)
+                        rc = srt;
+                }
+                if (rc != RADULS_OK)
+                    break;
+                ++timed;
+                if (!best.valid || ms_min < best_ms) {
+                    best = t;
+                    best_ms = ms_min;
+                }
+            }
+    g_force = nullptr;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RADULS_OK)
+        return rc;
+    {
+        std::lock_guard<std::mutex> g(g_tuned_mu);
+        g_tuned[dev][batched ? 1 : 0][rw] = best;
+    }
+    if (out) {
+        out->scatter_variant = best.scat_var;
+        out->scatter_tile = scatter_tile_of(best.scat_var);
+        out->block_cap = best.cap_b;
+        out->bucket_max = best.bucket_max;
+        out->best_ms = best_ms;
+        out->candidates = timed;
+    }
+    return RADULS_OK;
+}
+
+int raduls_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> g(g_tuned_mu);
+    for (auto &d : g_tuned)
+        for (auto &k : d)
+            for (auto &r : k)
+                r = Tuned{};
+    return RADULS_OK;
 }
 
 int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, uint32_t digit,

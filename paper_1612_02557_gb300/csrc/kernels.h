@@ -19,7 +19,7 @@ struct Shape {
     int bucket_var;  // mid-size bin kernel variant (-1: none for this record width)
 };
 
-Shape choose_shape(u32 rw, u32 key_words);
+Shape choose_shape(u32 rw, u32 key_words, bool batched = false);
 
 // Persistent-grid sizes (CTAs) of each kernel for a shape on the current device.
 u32 hist_grid(const Shape &s);
