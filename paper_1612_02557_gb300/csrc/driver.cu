@@ -1209,7 +1209,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     int vars[8];
     int nv = 0;
     for (int v = 0; v < 8; ++v)
-        if (scatter_variant_fits(v, rw) && !(v >= 3 && rw <= 4 && v != base.scat_var))
+        if (scatter_variant_fits(v, rw) && !((v == 3 || v == 4) && rw <= 4 && v != base.scat_var))
             vars[nv++] = v;
     const u32 caps[2] = {base.cap_b, base.cap_b / 2};
     const u32 bmaxes[3] = {0u, base.bucket_max / 2, base.bucket_max};
