@@ -24,182 +24,9 @@
 // chunk (the counting split of Sec. 1, with running offsets in shared memory),
 // and its sub-bins are sorted on chip group by group (onchip.cuh); sub-bins
 // too big for shared memory go on to the next level.
-#include "onchip.cuh"
+#include "midsize.cuh"
 
 namespace raduls {
-
-constexpr u32 CODE_WORDS = 32768;  // 65,536 16-bit counters, two per word
-constexpr u32 GROUP_MAX = 16;      // largest code group settled by ranking
-
-// Shared memory of the stable split (fallback path).
-template <int THREADS, int K, int KS>
-struct BucketSplitSmem {
-    BlockSmem<THREADS, K> b;           // on-chip sort scratch; b.xnew holds the split's permutation
-    u32 run[RADIX];                    // next slot of every sub-bin (relative to the bin)
-    u32 goff[RADIX];                   // run[d] - tstart[d] for the current chunk
-    u32 cbeg[RADIX + 1];               // sub-bin starts relative to the bin (cbeg[256] = count)
-    unsigned short glist[RADIX + 1];   // first sub-bin of every group
-    u32 gsum[RADIX / 32];
-    u32 ngroups;
-};
-
-// Shared memory of the code-group path.
-struct BucketCodeSmem {
-    u32 cnt[CODE_WORDS];                   // 16-bit counters -> group starts -> group ends
-    unsigned short oidx[BUCKET_IDX_MAX];   // original index of the record at each placed slot
-};
-
-template <int THREADS>
-struct BucketCommon {
-    static constexpr int NW = THREADS / 32;
-    u64 red_or[2][NW];
-    u64 red_and[2][NW];
-    u64 diff[MAX_KEY_WORDS];
-    u32 hist8[RADIX];   // records per value of the top varying digit
-    u32 wsum[NW];
-    u32 wmax[NW];
-    u32 item;
-    u32 maxc;
-    int t1, t2;         // the code's digits (t2 < 0: one varying digit only)
-};
-
-template <int THREADS, int K, int KS>
-constexpr size_t bucket_buf_words(u32 rw)
-{
-    // two split chunks (each with its 16-byte phase word) or one on-chip group
-    const size_t chunks = 2 * ((size_t)THREADS * KS * rw + 2);
-    const size_t group = (size_t)THREADS * K * rw + 2;
-    return (chunks > group ? chunks : group) + 2;
-}
-
-// Drop the L2 lines that lie wholly inside bytes [lo, hi) of global memory.
-template <int THREADS>
-__device__ __forceinline__ void discard_range(const void *lo, const void *hi)
-{
-    const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
-    for (uintptr_t x = a + (uintptr_t)threadIdx.x * 128; x < b; x += (uintptr_t)THREADS * 128)
-        discard_l2_line((const void *)x);
-}
-
-// L2 eviction policies (createpolicy): records read or written for the last
-// time leave L2 first; the private scratch copy stays until it is consumed.
-__device__ __forceinline__ u64 l2_evict_first()
-{
-    u64 p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ u64 l2_evict_last()
-{
-    u64 p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-template <int RW>
-__device__ __forceinline__ void load_rec_hint(u64 (&r)[RW], const u64 *g, u64 pol)
-{
-#pragma unroll
-    for (int i = 0; i < RW; i += 2) {
-        if (i + 1 < RW) {
-            asm volatile("ld.global.cg.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
-                         : "=l"(r[i]), "=l"(r[i + 1])
-                         : "l"(g + i), "l"(pol));
-        } else {
-            asm volatile("ld.global.cg.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r[i]) : "l"(g + i), "l"(pol));
-        }
-    }
-}
-
-template <int RW>
-__device__ __forceinline__ void store_rec_hint(u64 *g, const u64 (&r)[RW], u64 pol)
-{
-#pragma unroll
-    for (int i = 0; i < RW; i += 2) {
-        if (i + 1 < RW) {
-            asm volatile("st.global.L2::cache_hint.v2.u64 [%0], {%1, %2}, %3;" ::"l"(g + i), "l"(r[i]),
-                         "l"(r[i + 1]), "l"(pol)
-                         : "memory");
-        } else {
-            asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(g + i), "l"(r[i]), "l"(pol) : "memory");
-        }
-    }
-}
-
-// Word w of a record held in registers (unrolled select: no local memory).
-template <int RW>
-__device__ __forceinline__ u64 rec_word(const u64 (&r)[RW], u32 w)
-{
-    u64 x = r[0];
-#pragma unroll
-    for (int i = 1; i < RW; ++i)
-        if (w == (u32)i)
-            x = r[i];
-    return x;
-}
-
-template <int RW>
-__device__ __forceinline__ void load_rec(u64 (&r)[RW], const u64 *g)
-{
-    if constexpr (RW == 1) {
-        r[0] = __ldcg(g);
-    } else {
-#pragma unroll
-        for (int i = 0; i < RW; i += 2) {
-            const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2 *>(g + i));
-            r[i] = v.x;
-            r[i + 1] = v.y;
-        }
-    }
-}
-
-template <int RW>
-__device__ __forceinline__ void store_rec(u64 *g, const u64 (&r)[RW])
-{
-    if constexpr (RW == 1) {
-        g[0] = r[0];
-    } else {
-#pragma unroll
-        for (int i = 0; i < RW; i += 2)
-            *reinterpret_cast<ulonglong2 *>(g + i) = make_ulonglong2(r[i], r[i + 1]);
-    }
-}
-
-// Location of digit t: word and shift.
-struct DigitLoc {
-    u32 word, sh;
-};
-
-__device__ __forceinline__ DigitLoc digit_loc(u32 t, u32 key_words)
-{
-    return DigitLoc{key_words - 1u - t / 8u, 8u * (t % 8u)};
-}
-
-// 16-bit code of a record from its key words.
-__device__ __forceinline__ u32 code_of(u64 wa, u64 wb, const DigitLoc &la, const DigitLoc &lb, bool two)
-{
-    const u32 hi = (u32)(wa >> la.sh) & 0xffu;
-    const u32 lo = two ? (u32)(wb >> lb.sh) & 0xffu : 0u;
-    return (hi << 8) | lo;
-}
-
-__device__ __forceinline__ u32 get16(const u32 *cnt, u32 code)
-{
-    return (cnt[code >> 1] >> ((code & 1u) << 4)) & 0xffffu;
-}
-
-// Key order of two records of a bin (words below `w0` are equal): then the
-// original index decides.
-__device__ __forceinline__ bool rec_less(const u64 *x, const u64 *y, u32 ox, u32 oy, u32 w0, u32 key_words)
-{
-    for (u32 w = w0; w < key_words; ++w) {
-        const u64 a = __ldcg(x + w), b = __ldcg(y + w);
-        if (a != b)
-            return a < b;
-    }
-    return ox < oy;
-}
 
 // One mid-size bin by the code-group method (phases 1-4 above).  Returns 0
 // when the bin is sorted, or 1 + t1 when a code group is too large: the bin
@@ -211,9 +38,6 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
 {
     using Common = BucketCommon<THREADS>;
     constexpr int NW = THREADS / 32;
-    constexpr u32 CW = CODE_WORDS / THREADS;  // counter words per thread
-    static_assert(CODE_WORDS % THREADS == 0 && RADIX * 256 / (2 * CW) == THREADS,
-                  "four threads per value of the top digit");
     static_assert(RW >= 1, "compile-time record width");
     Common &cm = *reinterpret_cast<Common *>(smem_raw);
     BucketCodeSmem &cs = *reinterpret_cast<BucketCodeSmem *>(smem_raw + round16b(sizeof(Common)));
@@ -239,6 +63,8 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
     }
 
     // ---- 1. histogram of the code of digits (p, p-1), OR / AND of their words
+    if (tid < 32)
+        prefetch_l2_range(src, src + (u64)n * rw);
     for (u32 i = tid; i < CODE_WORDS; i += THREADS)
         cs.cnt[i] = 0;
     __syncthreads();
@@ -408,57 +234,17 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
     }
     const u32 t1 = (u32)cm.t1;
 
-    // ---- 2. group sizes: sums, largest group, the top digit's histogram
-    u32 sum = 0, mx = 0;
-    for (u32 j = 0; j < CW; ++j) {
-        const u32 v = cs.cnt[tid * CW + j];
-        const u32 lo = v & 0xffffu, hi = v >> 16;
-        sum += lo + hi;
-        mx = max(mx, max(lo, hi));
-    }
-    {
-        // four consecutive threads cover the 256 codes of one top-digit value
-        u32 s4 = sum + __shfl_down_sync(FULL_MASK, sum, 1);
-        s4 += __shfl_down_sync(FULL_MASK, s4, 2);
-        if ((tid & 3u) == 0)
-            cm.hist8[tid >> 2] = s4;
-        u32 incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const u32 v = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= (u32)o)
-                incl += v;
-        }
-        u32 wm = mx;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            wm = max(wm, __shfl_xor_sync(FULL_MASK, wm, o));
-        if (lane == 31)
-            cm.wsum[w] = incl;
-        if (lane == 0)
-            cm.wmax[w] = wm;
-        __syncthreads();
-        u32 before = 0, m2 = 0;
-        for (int i = 0; i < NW; ++i) {
-            before += (i < (int)w) ? cm.wsum[i] : 0u;
-            m2 = max(m2, cm.wmax[i]);
-        }
-        sum = before + incl - sum;  // exclusive start of this thread's codes
-        mx = m2;
-    }
+    // ---- 2. group sizes: total and largest group
+    u32 total, mx;
+    CodeScan<THREADS, CODE_WORDS>::totals(cs.cnt, cm.wsum, cm.wmax, total, mx);
+    (void)total;
 
     if (mx <= GROUP_MAX) {
         // this CTA's private scratch region (reused bin after bin, so it stays in L2)
         u64 *const scr = a.bucket_scratch + (u64)blockIdx.x * a.bucket_max * rw;
         const u64 pol_first = l2_evict_first(), pol_last = l2_evict_last();
         // ---- 3. placement by code (group starts -> running ends), original index kept
-        u32 run = sum;
-        for (u32 j = 0; j < CW; ++j) {
-            const u32 v = cs.cnt[tid * CW + j];
-            const u32 lo = v & 0xffffu, hi = v >> 16;
-            cs.cnt[tid * CW + j] = run | ((run + lo) << 16);
-            run += lo + hi;
-        }
+        CodeScan<THREADS, CODE_WORDS>::starts(cs.cnt, cm.wsum, 0u);
         __syncthreads();
         constexpr u32 U = RW >= 4 ? 2u : 4u;  // records in flight per thread
         for (u32 i0 = tid; i0 < n; i0 += THREADS * U) {

@@ -1,5 +1,5 @@
-"""GPU parity of the mid-size bin path (one CTA splits a bin through L2 and
-sorts its sub-bins on chip) against the CPU oracle, bit for bit.
+"""GPU parity of the mid-size bin path (one CTA sorts a bin through L2)
+against the CPU oracle, bit for bit.
 
 Inputs are built so that every branch of that kernel runs: bins at the first
 and at later levels, runs of small sub-bins, single sub-bins sorted by the
@@ -67,18 +67,23 @@ def _structured(kind: str, n: int, rec_bytes: int, key_bytes: int, seed: int) ->
     return recs
 
 
-def _sort_both_ways(recs: np.ndarray, key_bytes: int):
-    got = gpu_sort(recs, key_bytes)
-    old = os.environ.get("RADULS_BUCKET_MAX")
-    os.environ["RADULS_BUCKET_MAX"] = "0"
+def _with_env(name: str, value: str, fn):
+    old = os.environ.get(name)
+    os.environ[name] = value
     try:
-        off = gpu_sort(recs, key_bytes)
+        return fn()
     finally:
         if old is None:
-            del os.environ["RADULS_BUCKET_MAX"]
+            del os.environ[name]
         else:
-            os.environ["RADULS_BUCKET_MAX"] = old
-    return got, off
+            os.environ[name] = old
+
+
+def _sort_both_ways(recs: np.ndarray, key_bytes: int):
+    """The default settings and the mid-size path switched off (RADULS_BUCKET_MAX=0)."""
+    got = gpu_sort(recs, key_bytes)
+    off = _with_env("RADULS_BUCKET_MAX", "0", lambda: gpu_sort(recs, key_bytes))
+    return {"default": got, "off": off}
 
 
 @pytest.mark.parametrize("rec_bytes,key_bytes", [(8, 8), (16, 8), (32, 16), (24, 8), (16, 16)])
@@ -87,10 +92,10 @@ def test_mid_size_bins_match_oracle(oracle_mod, rec_bytes, key_bytes, n):
     if n > 100_000 and rec_bytes > 16:
         pytest.skip("large case on the main shapes only")
     recs = datagen.random_records(n, rec_bytes, key_bytes, n + rec_bytes)
-    got, off = _sort_both_ways(recs, key_bytes)
+    ways = _sort_both_ways(recs, key_bytes)
     want = oracle_mod.sort(recs, key_bytes, threads=8)
-    np.testing.assert_array_equal(got, want, err_msg=f"n={n} shape={rec_bytes},{key_bytes}")
-    np.testing.assert_array_equal(off, want)
+    for name, got in ways.items():
+        np.testing.assert_array_equal(got, want, err_msg=f"{name} n={n} shape={rec_bytes},{key_bytes}")
 
 
 @pytest.mark.parametrize("kind", ["spill", "mid_children", "last_digit", "last_digit_two_bins", "duplicates"])
@@ -98,10 +103,10 @@ def test_mid_size_bins_match_oracle(oracle_mod, rec_bytes, key_bytes, n):
                                                    (16, 8, 20_000)])
 def test_structured_keys_match_oracle(oracle_mod, kind, rec_bytes, key_bytes, n):
     recs = _structured(kind, n, rec_bytes, key_bytes, 11 + n % 97)
-    got, off = _sort_both_ways(recs, key_bytes)
+    ways = _sort_both_ways(recs, key_bytes)
     want = oracle_mod.sort(recs, key_bytes, threads=8)
-    np.testing.assert_array_equal(got, want, err_msg=f"{kind} n={n} shape={rec_bytes},{key_bytes}")
-    np.testing.assert_array_equal(off, want)
+    for name, got in ways.items():
+        np.testing.assert_array_equal(got, want, err_msg=f"{name} {kind} n={n} shape={rec_bytes},{key_bytes}")
 
 
 def test_stats_count_mid_size_bins(oracle_mod):
@@ -122,3 +127,4 @@ def test_stats_count_mid_size_bins(oracle_mod):
     assert st["hist_bytes_read"] == n * 16             # level 0 only: mid-size bins need no histogram pass
     assert st["kernel_launches"]["bucket"] >= 1
     np.testing.assert_array_equal(from_dev(d, n, 2), oracle_mod.sort(recs, 8, threads=8))
+
