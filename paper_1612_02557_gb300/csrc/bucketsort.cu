@@ -63,8 +63,6 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
     }
 
     // ---- 1. histogram of the code of digits (p, p-1), OR / AND of their words
-    if (tid < 32)
-        prefetch_l2_range(src, src + (u64)n * rw);
     for (u32 i = tid; i < CODE_WORDS; i += THREADS)
         cs.cnt[i] = 0;
     __syncthreads();

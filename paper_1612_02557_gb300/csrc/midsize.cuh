@@ -1,6 +1,6 @@
 // midsize.cuh -- pieces of the mid-size bin kernels (bucketsort.cu):
 // shared-memory layouts, the code-counter scan, digit and code helpers,
-// record loads and stores with L2 eviction and prefetch hints.
+// record loads and stores with L2 eviction hints.
 #pragma once
 
 #include "onchip.cuh"
@@ -57,21 +57,6 @@ __device__ __forceinline__ void discard_range(const void *lo, const void *hi)
     const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
     for (uintptr_t x = a + (uintptr_t)threadIdx.x * 128; x < b; x += (uintptr_t)THREADS * 128)
         discard_l2_line((const void *)x);
-}
-
-// Ask L2 to fetch bytes [lo, hi) of global memory, rounded inward to 16-byte
-// boundaries: bulk prefetches of up to 32 KB each, issued by the calling
-// warp's lanes (a hint -- nothing lands in the SM and nothing waits for it).
-// A phase that streams a bin turns from one round trip per batch of loads
-// into loads that find their lines in L2 or already on the way.
-__device__ __forceinline__ void prefetch_l2_range(const void *lo, const void *hi)
-{
-    constexpr uintptr_t PIECE = 32768;
-    const uintptr_t a = ((uintptr_t)lo + 15) & ~(uintptr_t)15, b = (uintptr_t)hi & ~(uintptr_t)15;
-    for (uintptr_t x = a + (uintptr_t)(threadIdx.x & 31u) * PIECE; x < b; x += 32 * PIECE) {
-        const u32 len = (u32)(b - x < PIECE ? b - x : PIECE);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(x), "r"(len) : "memory");
-    }
 }
 
 // L2 eviction policies (createpolicy): records read or written for the last
