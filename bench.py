@@ -65,7 +65,7 @@ WORKLOADS = {
 # its current code.
 DRAM_BYTES_PER_RECORD = {
     "scatter": (1.096104e9 + 1.048388e9) / 2 ** 26,   # profiles/scatter_uniform16.md (2^26 records)
-    "bucket": (533.259776e6 + 401.044224e6) / 1e7,    # profiles/bucket_uniform16.md (10^7 records)
+    "bucket": (399.890432e6 + 359.721728e6) / 1e7,    # profiles/bucket_uniform16.md (10^7 records)
 }
 # stats field holding each class's algorithmic bytes (read + write of every record it moves)
 CLASS_BYTES = {"scatter": "scatter_bytes", "bucket": "bucket_bytes", "block": "block_bytes",
