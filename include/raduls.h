@@ -111,6 +111,22 @@ typedef struct {
 int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                    const raduls_opts *opts, void *stream);
 
+/* End-to-end sort of records held in HOST memory (pinned or pageable):
+ * h_in's n_recs records are copied to device buffers the library owns (kept
+ * between calls and grown on demand to 2 x n_recs x rec_bytes), sorted there
+ * exactly as raduls_sort_ex sorts them (same options, same result), and
+ * copied back into h_out.  h_out may equal h_in (in place); otherwise the
+ * two ranges must not overlap.  Both copies are split into chunks spread over
+ * several copy streams so that more than one copy engine moves them.  The
+ * work is ordered on `stream` like every other call: h_in must stay unchanged
+ * and h_out untouched until the stream has passed the call (synchronise it,
+ * or call raduls_stream_status).  Pinned memory is much faster; pageable
+ * memory takes the driver's staging path.  No alignment rule for host
+ * pointers.  Errors as raduls_sort_ex, plus RADULS_ERR_OOM when the device
+ * buffers cannot be grown. */
+int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                     const raduls_opts *opts, void *stream);
+
 /* Sort n_segs independent arrays in one call.  Array s occupies records
  * [d_seg_offsets[s], d_seg_offsets[s+1]) of `in` (d_seg_offsets is a DEVICE
  * array of n_segs+1 non-decreasing u64 record offsets with d_seg_offsets[0]

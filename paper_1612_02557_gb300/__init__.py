@@ -11,7 +11,7 @@ from __future__ import annotations
 from ._lib import (RaduLSError, RaduLSModel, STATUS, build_library, library_path, load, raduls_autotune,
                    raduls_autotune_reset, raduls_debug_inject, raduls_distribution_pass, raduls_histogram,
                    raduls_histogram_static, raduls_set_wait_limit_ns, raduls_sort, raduls_sort_batched, raduls_sort_ex,
-                   raduls_status_string, raduls_stream_status)
+                   raduls_sort_host, raduls_status_string, raduls_stream_status)
 
 __all__ = [
     "RaduLSError",
@@ -23,6 +23,7 @@ __all__ = [
     "raduls_sort",
     "raduls_sort_ex",
     "raduls_sort_batched",
+    "raduls_sort_host",
     "raduls_autotune",
     "raduls_autotune_reset",
     "raduls_histogram",

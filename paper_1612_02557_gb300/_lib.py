@@ -104,6 +104,7 @@ def load():
             "raduls_sort": [vp, vp, u64, u32, u32, vp],
             "raduls_sort_ex": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_sort_batched": [vp, vp, vp, u32, u32, u32, vp],
+            "raduls_sort_host": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_autotune": [vp, vp, u64, u32, u32, vp, u32, vp, vp],
             "raduls_autotune_reset": [],
             "raduls_histogram": [vp, u64, u32, u32, u32, vp, vp],
@@ -195,6 +196,46 @@ def raduls_sort_ex(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, mode: 
     rc = load().raduls_sort_ex(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes, ctypes.byref(o),
                                _stream(stream, in_, tmp))
     _raise(rc, "raduls_sort_ex")
+    return st.as_dict() if stats else None
+
+
+def _host_addr(x, writable: bool) -> tuple[int, int]:
+    """(address, bytes) of a host buffer: a CPU torch tensor or a numpy array."""
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda:
+            raise ValueError("raduls_sort_host takes host buffers")
+        if not x.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return int(x.data_ptr()), int(x.numel() * x.element_size())
+    iface = getattr(x, "__array_interface__", None)
+    if iface is None:
+        raise TypeError(f"expected a CPU tensor or a numpy array, got {type(x)}")
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("buffers must be contiguous")
+    if writable and iface["data"][1]:
+        raise ValueError("the output buffer must be writable")
+    return int(iface["data"][0]), int(x.nbytes)
+
+
+def raduls_sort_host(h_in, h_out, n_recs: int, rec_bytes: int, key_bytes: int, mode: str = "auto",
+                     learned_log2_buckets: int = 0, fallback_ratio: float = 0.0, train_steps: int = 0,
+                     stats: bool = False, stream=None) -> dict | None:
+    """Sort host records end to end (copy in, sort, copy out) through the C
+    ABI; h_out may be h_in.  Ordered on `stream` (default: the current CUDA
+    stream): synchronise before reading h_out."""
+    a_in, nb_in = _host_addr(h_in, False)
+    a_out, nb_out = _host_addr(h_out, True)
+    need = n_recs * rec_bytes
+    if nb_in < need or nb_out < need:
+        raise ValueError(f"host buffers hold {nb_in} and {nb_out} bytes, need {need}")
+    st = Stats()
+    o = Opts(MODES[mode], learned_log2_buckets, fallback_ratio, train_steps,
+             ctypes.pointer(st) if stats else None)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    rc = load().raduls_sort_host(a_in, a_out, n_recs, rec_bytes, key_bytes, ctypes.byref(o), _stream(stream))
+    _raise(rc, "raduls_sort_host")
     return st.as_dict() if stats else None
 
 

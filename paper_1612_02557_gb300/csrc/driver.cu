@@ -6,6 +6,7 @@
 // distribution launch for all big bins of the level -- until no bin is bigger
 // than what one CTA sorts on chip, then copies back finished bins left in the
 // scratch buffer and runs the on-chip sorts of all small-bin runs.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -155,12 +156,18 @@ struct ModelBufs {
     u32 log2b = 0;
 };
 
+constexpr int COPY_STREAMS_MAX = 8;
+
 struct Ctx {
     std::mutex mu;
     bool inited = false;
     u32 *dev_status = nullptr;   // device: sticky status word of this device
     Work main, aux;
     ModelBufs mdl;
+    DevBuf host_in, host_tmp;    // raduls_sort_host: the device copy of the records and its scratch
+    cudaStream_t copy_st[COPY_STREAMS_MAX] = {};
+    cudaEvent_t copy_ev[COPY_STREAMS_MAX + 1] = {};
+    bool have_copy = false;
     u64 wait_ns = 2000000000ull;
     u32 inject_tile = ~0u;
     cudaEvent_t ev[1024] = {};
@@ -986,6 +993,100 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
 int raduls_sort(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, void *stream)
 {
     return raduls_sort_ex(in, tmp, n_recs, rec_bytes, key_bytes, nullptr, stream);
+}
+
+int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                     const raduls_opts *opts, void *stream)
+{
+    int rc = check_args(nullptr, nullptr, 0, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n_recs > 0 && (!h_in || !h_out))
+        return RADULS_ERR_INVALID_ARG;
+    if (n_recs > (1ull << 39) || n_recs > (~0ull) / rec_bytes)
+        return RADULS_ERR_UNSUPPORTED;
+    if (opts && (opts->mode > 2u ||
+                 (opts->learned_log2_buckets && (opts->learned_log2_buckets < 12u || opts->learned_log2_buckets > 16u))))
+        return RADULS_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)n_recs * rec_bytes;
+    if (h_in != h_out && n_recs > 0) {
+        const uintptr_t a = (uintptr_t)h_in, b = (uintptr_t)h_out;
+        if (a < b + bytes && b < a + bytes)
+            return RADULS_ERR_INVALID_ARG;
+    }
+    if (opts && opts->stats)
+        std::memset(opts->stats, 0, sizeof(raduls_stats));
+    if (n_recs == 0)
+        return RADULS_OK;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaError_t e = ctx_init(*c);
+    if (e != cudaSuccess)
+        return to_status(e);
+    int ns = 4;
+    if (const char *v = getenv("RADULS_COPY_STREAMS"))
+        ns = atoi(v);
+    ns = ns < 1 ? 1 : ns > COPY_STREAMS_MAX ? COPY_STREAMS_MAX : ns;
+    if (!c->have_copy) {
+        for (int i = 0; i < COPY_STREAMS_MAX; ++i)
+            CK(cudaStreamCreateWithFlags(&c->copy_st[i], cudaStreamNonBlocking));
+        for (int i = 0; i <= COPY_STREAMS_MAX; ++i)
+            CK(cudaEventCreateWithFlags(&c->copy_ev[i], cudaEventDisableTiming));
+        c->have_copy = true;
+    }
+    e = ensure(c->host_in, bytes, false);
+    if (e == cudaSuccess)
+        e = ensure(c->host_tmp, bytes, false);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? RADULS_ERR_OOM : to_status(e);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *d = (unsigned char *)c->host_in.p;
+    // chunks of at least 64 MiB, dealt round-robin to the copy streams; each
+    // copy stream starts after the work already on `stream`, and `stream`
+    // continues after every copy stream
+    const size_t chunk = std::max<size_t>((size_t)64 << 20, (bytes + 4 * ns - 1) / (4 * ns));
+    auto spread = [&](bool to_dev) -> cudaError_t {
+        cudaError_t x = cudaEventRecord(c->copy_ev[COPY_STREAMS_MAX], st);
+        for (int i = 0; i < ns && x == cudaSuccess; ++i)
+            x = cudaStreamWaitEvent(c->copy_st[i], c->copy_ev[COPY_STREAMS_MAX], 0);
+        int k = 0;
+        for (size_t off = 0; off < bytes && x == cudaSuccess; off += chunk, k = (k + 1) % ns) {
+            const size_t len = std::min(chunk, bytes - off);
+            x = to_dev ? cudaMemcpyAsync(d + off, (const unsigned char *)h_in + off, len, cudaMemcpyHostToDevice,
+                                         c->copy_st[k])
+                       : cudaMemcpyAsync((unsigned char *)h_out + off, d + off, len, cudaMemcpyDeviceToHost,
+                                         c->copy_st[k]);
+        }
+        for (int i = 0; i < ns && x == cudaSuccess; ++i) {
+            x = cudaEventRecord(c->copy_ev[i], c->copy_st[i]);
+            if (x == cudaSuccess)
+                x = cudaStreamWaitEvent(st, c->copy_ev[i], 0);
+        }
+        return x;
+    };
+    e = spread(true);
+    if (e != cudaSuccess)
+        return to_status(e);
+    if (n_recs > 1) {
+        SortJob j{};
+        j.in = (u64 *)c->host_in.p;
+        j.tmp = (u64 *)c->host_tmp.p;
+        j.n = n_recs;
+        j.rw = rec_bytes / 8u;
+        j.kw = key_bytes / 8u;
+        j.stats = opts ? opts->stats : nullptr;
+        j.mode = opts ? opts->mode : 0u;
+        j.log2b = opts ? opts->learned_log2_buckets : 0u;
+        j.fallback_ratio = opts ? opts->fallback_ratio : 0.f;
+        j.train_steps = (opts && opts->train_steps) ? opts->train_steps : 16u;
+        rc = run_sort(*c, c->main, j, st);
+        if (rc)
+            return rc;
+    }
+    e = spread(false);
+    return to_status(e);
 }
 
 int raduls_model_fit(raduls_model **out, const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
