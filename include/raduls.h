@@ -116,8 +116,10 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
  * between calls and grown on demand to 2 x n_recs x rec_bytes), sorted there
  * exactly as raduls_sort_ex sorts them (same options, same result), and
  * copied back into h_out.  h_out may equal h_in (in place); otherwise the
- * two ranges must not overlap.  Both copies are split into chunks spread over
- * several copy streams so that more than one copy engine moves them.  The
+ * two ranges must not overlap.  Both copies run on the library's own copy
+ * stream, in chunks (the environment variable RADULS_COPY_STREAMS spreads
+ * them over up to 8 streams; on GB300 one stream already moves about 200 GB/s
+ * each way, the link's rate, and more streams were slower).  The
  * work is ordered on `stream` like every other call: h_in must stay unchanged
  * and h_out untouched until the stream has passed the call (synchronise it,
  * or call raduls_stream_status).  Pinned memory is much faster; pageable

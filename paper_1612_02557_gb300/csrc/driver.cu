@@ -1025,7 +1025,7 @@ int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t re
     cudaError_t e = ctx_init(*c);
     if (e != cudaSuccess)
         return to_status(e);
-    int ns = 4;
+    int ns = 1;  // one copy stream reaches the host link's rate; more were slower
     if (const char *v = getenv("RADULS_COPY_STREAMS"))
         ns = atoi(v);
     ns = ns < 1 ? 1 : ns > COPY_STREAMS_MAX ? COPY_STREAMS_MAX : ns;
