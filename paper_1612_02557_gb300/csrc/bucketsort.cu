@@ -239,7 +239,8 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
 
     if (mx <= GROUP_MAX) {
         // this CTA's private scratch region (reused bin after bin, so it stays in L2)
-        u64 *const scr = a.bucket_scratch + (u64)blockIdx.x * a.bucket_max * rw;
+        constexpr u32 SW = slot_words<RW>();  // scratch words per record
+        u64 *const scr = a.bucket_scratch + (u64)blockIdx.x * a.bucket_max * SW;
         const u64 pol_first = l2_evict_first(), pol_last = l2_evict_last();
         // ---- 3. placement by code (group starts -> running ends), original index kept
         CodeScan<THREADS, CODE_WORDS>::starts(cs.cnt, cm.wsum, 0u);
@@ -261,7 +262,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
                     const u32 sh = (c & 1u) << 4;
                     const u32 pos = (atomicAdd(&cs.cnt[c >> 1], 1u << sh) >> sh) & 0xffffu;
                     if (pos < n) {
-                        store_rec_hint<RW>(scr + (u64)pos * rw, r[k], pol_last);
+                        store_slot_hint<RW>(scr + (u64)pos * SW, r[k], pol_last);
                         cs.oidx[pos] = (unsigned short)i;
                     } else {
                         set_error(a.ctrs, ST_INTERNAL);
@@ -283,7 +284,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
 #pragma unroll
             for (u32 k = 0; k < U4; ++k)
                 if (q0 + k * THREADS < n)
-                    load_rec_hint<RW>(rr[k], scr + (u64)(q0 + k * THREADS) * rw, pol_first);
+                    load_rec_hint<RW>(rr[k], scr + (u64)(q0 + k * THREADS) * SW, pol_first);
 #pragma unroll
             for (u32 k = 0; k < U4; ++k) {
                 const u32 q = q0 + k * THREADS;
@@ -312,7 +313,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
                         if (kx != kq)
                             lt = kx < kq;
                         else if (w0 + 1 < key_words)
-                            lt = rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, ox, oq, w0 + 1, key_words);
+                            lt = rec_less(scr + (u64)(s + j) * SW, scr + (u64)q * SW, ox, oq, w0 + 1, key_words);
                         else
                             lt = ox < oq;
                         rank += lt ? 1u : 0u;
@@ -325,7 +326,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
                         u64 km[4];
 #pragma unroll
                         for (u32 jj = 0; jj < 4; ++jj)
-                            km[jj] = j0 + jj < g ? __ldcg(scr + (u64)(s + j0 + jj) * rw + w0) : 0ull;
+                            km[jj] = j0 + jj < g ? __ldcg(scr + (u64)(s + j0 + jj) * SW + w0) : 0ull;
 #pragma unroll
                         for (u32 jj = 0; jj < 4; ++jj) {
                             const u32 j = j0 + jj;
@@ -334,7 +335,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
                                 if (km[jj] != kq)
                                     lt = km[jj] < kq;
                                 else
-                                    lt = rec_less(scr + (u64)(s + j) * rw, scr + (u64)q * rw, cs.oidx[s + j], oq,
+                                    lt = rec_less(scr + (u64)(s + j) * SW, scr + (u64)q * SW, cs.oidx[s + j], oq,
                                                   w0 + 1, key_words);
                                 rank += lt ? 1u : 0u;
                             }
@@ -347,7 +348,7 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
         }
         __syncthreads();
         // the scratch copy is dead: drop it from L2 unwritten
-        discard_range<THREADS>(scr, scr + (u64)n * rw);
+        discard_range<THREADS>(scr, scr + (u64)n * SW);
         __syncthreads();
         return 0;
     }

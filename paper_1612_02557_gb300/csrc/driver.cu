@@ -595,7 +595,7 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
     const bool may_learn = !step_api && j.mode != 1 && j.n > s.cap_b;
     const u32 bmax = step_api ? 0u : s.bucket_max;
     if (bmax)
-        CK(ensure(wk.bscratch, (size_t)bucket_grid() * bmax * j.rw * 8, false));
+        CK(ensure(wk.bscratch, (size_t)bucket_grid() * bmax * bucket_slot_bytes(j.rw), false));
     TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, step_api ? j.digit : top,
                                       s.cap_b, s.tile_h, step_api ? 1u : 0u, L.bkt[0], bmax, st));
     {
@@ -843,7 +843,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
     LevelBufs B{};
     CK(work_level(wk, s, n, L.caps.grid, B, L.caps, st));
     if (s.bucket_max)
-        CK(ensure(wk.bscratch, (size_t)bucket_grid() * s.bucket_max * rw * 8, false));
+        CK(ensure(wk.bscratch, (size_t)bucket_grid() * s.bucket_max * bucket_slot_bytes(rw), false));
     // the persistent kernel's queue: mid-size arrays (<= n_segs), pushed items
     // (each a sub-bin of more than one on-chip group), ready flags
     BatchQueue q{};

@@ -61,11 +61,14 @@ struct PlanArgs {
     WorkItem *buckets_next;  // mid-size bins found in this level (sorted in the next one)
     WorkItem *buckets_split; // mid-size bins of this level with heavy code groups (stable split)
     u32 bucket_max;          // bins of plain digits with count <= bucket_max go there (0: never)
-    u64 *bucket_scratch;     // bucket_max * rw words per CTA of the mid-size bin kernel
+    u64 *bucket_scratch;     // bucket_max record slots per CTA of the mid-size bin kernel (bucket_slot_bytes each)
 };
 
 // CTAs of the mid-size bin kernel (one per SM): its scratch holds that many regions.
 u32 bucket_grid();
+// Bytes of one record's slot in a mid-size CTA's scratch region (16-byte
+// records take a whole 32-byte sector; see slot_words in midsize.cuh).
+inline size_t bucket_slot_bytes(u32 rw) { return rw == 2 ? 32u : (size_t)rw * 8u; }
 
 __device__ __forceinline__ u32 ceil_div_u64(u64 a, u32 b) { return (u32)((a + b - 1) / b); }
 

@@ -105,6 +105,27 @@ __device__ __forceinline__ void store_rec_hint(u64 *g, const u64 (&r)[RW], u64 p
     }
 }
 
+// Scratch slot of a record: 16-byte records get a 32-byte slot, written whole
+// (one 256-bit store fills the sector), because the placement writes land at
+// scattered slots and a half-written sector costs more than a full one.
+template <int RW>
+constexpr u32 slot_words()
+{
+    return RW == 2 ? 4u : (u32)RW;
+}
+
+template <int RW>
+__device__ __forceinline__ void store_slot_hint(u64 *g, const u64 (&r)[RW], u64 pol)
+{
+    if constexpr (RW == 2) {
+        asm volatile("st.global.L2::cache_hint.v4.b64 [%0], {%1, %2, %3, %4}, %5;" ::"l"(g), "l"(r[0]), "l"(r[1]),
+                     "l"(0ull), "l"(0ull), "l"(pol)
+                     : "memory");
+    } else {
+        store_rec_hint<RW>(g, r, pol);
+    }
+}
+
 // Word w of a record held in registers (unrolled select: no local memory).
 template <int RW>
 __device__ __forceinline__ u64 rec_word(const u64 (&r)[RW], u32 w)
