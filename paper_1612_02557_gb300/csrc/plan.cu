@@ -56,7 +56,7 @@ __device__ void append_block(const PlanArgs &a, u64 begin, u64 count, u32 digit,
     a.blocks[slot] = it;
 }
 
-// Next digit below p that varies inside the bin, judged from the OR and AND of
+// Next digit below p that varies inside the bin, decided from the OR and AND of
 // the key word holding p (bytes where they differ vary).  Returns -1 when no
 // digit is left.  When the rest of this word is constant, the top digit of the
 // next word is returned: its own histogram will tell.
