@@ -364,15 +364,17 @@ bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BucketCommon<THREADS> &cm = *reinterpret_cast<BucketCommon<THREADS> *>(smem_raw);
-    const u32 n_items = a.ctrs->bucket_cur;
+    // the whole list, or one position window of it
+    const u32 first = a.bucket_order ? a.bucket_wstart[a.bucket_window] : 0u;
+    const u32 n_items = a.bucket_order ? a.bucket_wstart[a.bucket_window + 1] : a.ctrs->bucket_cur;
     for (;;) {
         if (threadIdx.x == 0)
-            cm.item = atomicAdd(&a.ctrs->tile_ctr[4], 1u);
+            cm.item = first + atomicAdd(&a.ctrs->tile_ctr[4], 1u);
         __syncthreads();
         const u32 ii = cm.item;
         if (ii >= n_items)
             break;
-        const WorkItem item = a.buckets_cur[ii];
+        const WorkItem item = a.buckets_cur[a.bucket_order ? a.bucket_order[ii] : ii];
         const int rc = bucket_code_item<THREADS, RW>(smem_raw, in, tmp, a, item);
         if (rc > 0 && threadIdx.x == 0) {
             // heavy code groups: the stable split (bucket_split_kernel) takes the bin

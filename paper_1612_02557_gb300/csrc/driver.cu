@@ -142,6 +142,7 @@ struct Work {
     DevBuf lists, hist, status, tiles;
     DevBuf bscratch;  // private scratch regions of the mid-size bin kernel's CTAs
     DevBuf bqueue;    // batched persistent kernel: mid-size array list, pushed items, ready flags
+    DevBuf win;       // end-to-end sort: mid-size bins grouped by position window
 };
 
 // Device buffers of one learned model (see the Model struct in common.cuh).
@@ -167,6 +168,7 @@ struct Ctx {
     DevBuf host_in, host_tmp;    // raduls_sort_host: the device copy of the records and its scratch
     cudaStream_t copy_st[COPY_STREAMS_MAX] = {};
     cudaEvent_t copy_ev[COPY_STREAMS_MAX + 1] = {};
+    cudaEvent_t win_ev[BUCKET_WINDOWS_MAX] = {};
     bool have_copy = false;
     u64 wait_ns = 2000000000ull;
     u32 inject_tile = ~0u;
@@ -428,6 +430,32 @@ struct SortJob {
     u32 log2b;             // learned buckets (0 = chosen from n)
     float fallback_ratio;  // learned partition rejected above this
     u32 train_steps;
+    struct HostOut *hout;  // end-to-end sort: where the sorted records go on the host
+};
+
+// Destination of an end-to-end sort (raduls_sort_host).  The last mid-size
+// level runs window by window; after each window the records before the next
+// window's first position are final and go back to the host on the copy
+// stream while the next window is sorted.  `copied` stays set only if nothing
+// writes the records afterwards (no on-chip or copy-back items, no later level).
+struct HostOut {
+    unsigned char *dst;
+    const unsigned char *src;   // the device copy being sorted
+    u32 rec_bytes;
+    cudaStream_t cst;
+    cudaEvent_t *ev;            // BUCKET_WINDOWS_MAX events
+    bool copied;
+
+    cudaError_t copy(u64 lo, u64 hi, u32 w, cudaStream_t st)
+    {
+        cudaError_t e = cudaEventRecord(ev[w], st);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(cst, ev[w], 0);
+        if (e == cudaSuccess && hi > lo)
+            e = cudaMemcpyAsync(dst + lo * rec_bytes, src + lo * rec_bytes, (size_t)(hi - lo) * rec_bytes,
+                                cudaMemcpyDeviceToHost, cst);
+        return e;
+    }
 };
 
 #define CK(x)                               \
@@ -685,8 +713,32 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
                                                    wk.epoch, c.wait_ns, c.inject_tile, model, st));
             c.inject_tile = ~0u;
         }
-        if (n_bkt > 0)
+        if (n_bkt > 0 && n_grid == 0 && j.hout && !wk.h_ctrs->block && !wk.h_ctrs->copy) {
+            // the last mid-size level of an end-to-end sort: position windows,
+            // each copied back while the next is sorted
+            const u32 nw = BUCKET_WINDOWS_MAX;
+            CK(ensure(wk.win, ((size_t)n_bkt + nw + 1) * 4, false));
+            u32 *const order = (u32 *)wk.win.p, *const wstart = order + n_bkt;
+            TIMED(RADULS_K_SETUP, launch_bucket_windows(L.bkt[cur], wk.ctrs, j.n, nw, order, wstart, st));
+            a.bucket_order = order;
+            a.bucket_wstart = wstart;
+            for (u32 w = 0; w < nw; ++w) {
+                if (w > 0)
+                    TIMED(RADULS_K_SETUP, launch_bucket_window_reset(wk.ctrs, st));
+                a.bucket_window = w;
+                TIMED(RADULS_K_BUCKET, launch_bucket(s, j.in, j.tmp, a, st));
+                // bins starting at or after position ceil((w + 1) n / nw) belong to
+                // later windows, so everything before floor((w + 1) n / nw) is final
+                CK(j.hout->copy(j.n * w / nw, w + 1 == nw ? j.n : j.n * (w + 1) / nw, w, st));
+            }
+            j.hout->copied = true;
+        } else if (n_bkt > 0) {
+            if (j.hout)
+                j.hout->copied = false;  // a level after the windows: copy everything at the end
             TIMED(RADULS_K_BUCKET, launch_bucket(s, j.in, j.tmp, a, st));
+        }
+        if (n_grid > 0 && j.hout)
+            j.hout->copied = false;
         TIMED(RADULS_K_SETUP, launch_advance(wk.ctrs, st));
         if (j.single_pass)
             break;
@@ -698,6 +750,8 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         n_bkt = wk.h_ctrs->bucket_cur;
         cur ^= 1;
     }
+    if (j.hout && (wk.h_ctrs->block || wk.h_ctrs->copy || wk.h_ctrs->err))
+        j.hout->copied = false;  // records still move after the last level
     if (!step_api) {
         TIMED(RADULS_K_COPY, launch_copy(s, j.in, j.tmp, L.copies, L.tile_copy, wk.ctrs, st));
         TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks, wk.ctrs, nullptr, st));
@@ -1034,6 +1088,8 @@ int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t re
             CK(cudaStreamCreateWithFlags(&c->copy_st[i], cudaStreamNonBlocking));
         for (int i = 0; i <= COPY_STREAMS_MAX; ++i)
             CK(cudaEventCreateWithFlags(&c->copy_ev[i], cudaEventDisableTiming));
+        for (u32 i = 0; i < BUCKET_WINDOWS_MAX; ++i)
+            CK(cudaEventCreateWithFlags(&c->win_ev[i], cudaEventDisableTiming));
         c->have_copy = true;
     }
     e = ensure(c->host_in, bytes, false);
@@ -1081,9 +1137,19 @@ int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t re
         j.log2b = opts ? opts->learned_log2_buckets : 0u;
         j.fallback_ratio = opts ? opts->fallback_ratio : 0.f;
         j.train_steps = (opts && opts->train_steps) ? opts->train_steps : 16u;
+        HostOut ho{(unsigned char *)h_out, d, rec_bytes, c->copy_st[0], c->win_ev, false};
+        const char *wv = getenv("RADULS_HOST_WINDOWS");  // "0": copy back only after the whole sort
+        j.hout = (wv && atoi(wv) == 0) ? nullptr : &ho;
         rc = run_sort(*c, c->main, j, st);
         if (rc)
             return rc;
+        if (ho.copied) {
+            // every record went back window by window: `stream` continues after the last copy
+            e = cudaEventRecord(c->copy_ev[0], c->copy_st[0]);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(st, c->copy_ev[0], 0);
+            return to_status(e);
+        }
     }
     e = spread(false);
     return to_status(e);

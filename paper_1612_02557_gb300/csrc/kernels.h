@@ -62,7 +62,14 @@ struct PlanArgs {
     WorkItem *buckets_split; // mid-size bins of this level with heavy code groups (stable split)
     u32 bucket_max;          // bins of plain digits with count <= bucket_max go there (0: never)
     u64 *bucket_scratch;     // bucket_max record slots per CTA of the mid-size bin kernel (bucket_slot_bytes each)
+    const u32 *bucket_order;  // non-null: the mid-size kernel takes only window bucket_window of this list
+    const u32 *bucket_wstart; // (bin indices grouped by position window; see launch_bucket_windows)
+    u32 bucket_window;
 };
+
+// Position windows of the last mid-size level (an end-to-end sort copies each
+// window back to the host while the next one is sorted).
+constexpr u32 BUCKET_WINDOWS_MAX = 8;
 
 // CTAs of the mid-size bin kernel (one per SM): its scratch holds that many regions.
 u32 bucket_grid();
@@ -142,6 +149,9 @@ cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs
                         cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
+cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
+                                  u32 *wstart, cudaStream_t st);
+cudaError_t launch_bucket_window_reset(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
                                 Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
                                 u32 bucket_max, cudaStream_t st);

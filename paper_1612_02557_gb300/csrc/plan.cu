@@ -467,6 +467,65 @@ cudaError_t launch_advance(Counters *ctrs, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Mid-size bins of this level grouped by position window: window w holds the
+// bins whose first record lies in [w n / nw, (w + 1) n / nw).  order[] lists
+// bin indices window by window (any order inside a window), wstart[w] is
+// where window w starts in order[] (wstart[nw] = number of bins).
+__global__ void __launch_bounds__(1024)
+bucket_window_kernel(const WorkItem *__restrict__ items, const Counters *__restrict__ ctrs, u64 n, u32 nw,
+                     u32 *__restrict__ order, u32 *__restrict__ wstart)
+{
+    __shared__ u32 cnt[BUCKET_WINDOWS_MAX], pos[BUCKET_WINDOWS_MAX];
+    const u32 m = ctrs->bucket_cur;
+    const u32 tid = threadIdx.x;
+    auto win_of = [&](u64 b) {
+        const u64 w = n ? b * nw / n : 0;
+        return (u32)(w < nw ? w : nw - 1u);
+    };
+    if (tid < BUCKET_WINDOWS_MAX)
+        cnt[tid] = 0;
+    __syncthreads();
+    for (u32 i = tid; i < m; i += blockDim.x)
+        atomicAdd(&cnt[win_of(items[i].begin)], 1u);
+    __syncthreads();
+    if (tid == 0) {
+        u32 acc = 0;
+        for (u32 w = 0; w < nw; ++w) {
+            wstart[w] = acc;
+            pos[w] = acc;
+            acc += cnt[w];
+        }
+        wstart[nw] = acc;
+    }
+    __syncthreads();
+    for (u32 i = tid; i < m; i += blockDim.x)
+        order[atomicAdd(&pos[win_of(items[i].begin)], 1u)] = i;
+}
+
+// Before the next window: the mid-size kernel's item counter and this level's
+// stable-split list start over (the previous window's split items are done).
+__global__ void bucket_window_reset_kernel(Counters *c)
+{
+    c->tile_ctr[4] = 0;
+    c->bucket_split = 0;
+    c->split_ctr = 0;
+}
+
+cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
+                                  u32 *wstart, cudaStream_t st)
+{
+    if (nw < 1 || nw > BUCKET_WINDOWS_MAX)
+        return cudaErrorInvalidValue;
+    bucket_window_kernel<<<1, 1024, 0, st>>>(items, ctrs, n, nw, order, wstart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_window_reset(Counters *ctrs, cudaStream_t st)
+{
+    bucket_window_reset_kernel<<<1, 1, 0, st>>>(ctrs);
+    return cudaGetLastError();
+}
+
 u32 copy_grid()
 {
     int dev = 0, sms = 0;

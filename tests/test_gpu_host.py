@@ -90,3 +90,21 @@ def test_bad_arguments_are_refused():
         p.raduls_sort_host(buf[:64], buf[1:], 64, 16, 8)     # partly overlapping ranges: refused by the library
     with pytest.raises(p.RaduLSError):
         p.raduls_sort_host(buf, buf, 65, 12, 8)              # record size not a multiple of 8
+
+
+@pytest.mark.parametrize("windows", ["1", "0"])
+def test_window_copy_back_on_and_off(oracle_mod, windows, monkeypatch):
+    """The last mid-size level copied back window by window (default) and the
+    whole array copied after the sort (RADULS_HOST_WINDOWS=0) give the same
+    bytes: 2^23 + 12,345 uniform records end in 256 mid-size bins (the
+    windowed case; windows do not fall on bin boundaries)."""
+    import torch
+    p = lib()
+    monkeypatch.setenv("RADULS_HOST_WINDOWS", windows)
+    n = (1 << 23) + 12_345
+    recs = datagen.WORKLOADS["uniform16"](n)
+    h_in = torch.from_numpy(recs.view(np.int64)).pin_memory()
+    h_out = torch.zeros_like(h_in).pin_memory()
+    p.raduls_sort_host(h_in, h_out, n, 16, 8, mode="plain")
+    assert p.raduls_stream_status() == 0
+    np.testing.assert_array_equal(h_out.numpy().view(np.uint64), oracle_mod.sort(recs, 8, threads=8))
