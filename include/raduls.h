@@ -252,7 +252,10 @@ typedef struct {
  * record width, the on-chip class at its full and half capacity, the
  * mid-size class off, at half and at full size -- with `tmp` as scratch,
  * times each with CUDA events (best of two), and keeps the fastest for later
- * calls on this device with this record width: plain sorts when
+ * calls on this device with this record width (candidates go from the default
+ * shape outward, and one must beat the current choice by more than 1% to
+ * replace it, so timing noise never trades the default size classes for
+ * smaller ones that only uniform keys tolerate): plain sorts when
  * d_seg_offsets is NULL, batched sorts (with those offsets) otherwise.  The
  * digit width stays 8 bits.  `in` and `tmp` hold n_recs records; their
  * contents are undefined afterwards.  Synchronises `stream`; not for use

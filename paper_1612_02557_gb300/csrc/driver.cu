@@ -1373,13 +1373,20 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     g_force = &none;
     const Shape base = choose_shape(rw, kw, batched);
     g_force = nullptr;
+    // Candidates go from the default shape outward (its distribution variant
+    // first, the full size classes first), and a later one must beat the
+    // current choice by more than TIE_FRAC: within timing noise the default,
+    // larger size classes stay, which suits inputs less regular than the
+    // tuner's seeded records.
+    constexpr float TIE_FRAC = 0.01f;
     int vars[8];
     int nv = 0;
+    vars[nv++] = base.scat_var;
     for (int v = 0; v < 8; ++v)
-        if (scatter_variant_fits(v, rw) && !((v == 3 || v == 4) && rw <= 4 && v != base.scat_var))
+        if (v != base.scat_var && scatter_variant_fits(v, rw) && !((v == 3 || v == 4) && rw <= 4))
             vars[nv++] = v;
     const u32 caps[2] = {base.cap_b, base.cap_b / 2};
-    const u32 bmaxes[3] = {0u, base.bucket_max / 2, base.bucket_max};
+    const u32 bmaxes[3] = {base.bucket_max, base.bucket_max / 2, 0u};
     const int nb = base.bucket_max ? 3 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1398,8 +1405,8 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
                 t.scat_var = vars[vi];
                 t.cap_b = caps[ci];
                 t.bucket_max = bmaxes[bi] > caps[ci] ? bmaxes[bi] : 0u;
-                if (bi > 0 && t.bucket_max == 0)
-                    continue;
+                if (bmaxes[bi] != 0u && t.bucket_max == 0)
+                    continue;  // collapses to "off", which is a candidate of its own
                 float ms_min = 0.f;
                 for (int rep = 0; rep < 2 && rc == RADULS_OK; ++rep) {
                     tune_fill_kernel<<<1024, 256, 0, st>>>((u64 *)in, n_recs * rw, 0x5241445553ull + rep);
@@ -1448,7 +1455,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
                 if (rc != RADULS_OK)
                     break;
                 ++timed;
-                if (!best.valid || ms_min < best_ms) {
+                if (!best.valid || ms_min < best_ms * (1.f - TIE_FRAC)) {
                     best = t;
                     best_ms = ms_min;
                 }
