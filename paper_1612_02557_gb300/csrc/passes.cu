@@ -143,6 +143,8 @@ struct ScatterSmem {
     u64 excl[RADIX];              // records of each digit in earlier tiles of the bin
     u32 total[RADIX];             // this tile's records of each digit
     u32 perm[THREADS * K];        // tile-sorted slot -> element | digit << 16
+    WorkItem item;                // the item of the tile in hand (thread 0 copies it in)
+    u32 item_idx;                 // its index in the item list (~0u: none yet)
     u32 tile;
     u32 abort;
 };
@@ -224,16 +226,28 @@ scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__re
     const u32 n_tiles = ctrs->scatter_tiles;
     const u32 ep = *epoch & LB_EPOCH_MASK;
 
+    if (tid == 0)
+        sm.item_idx = ~0u;
     for (;;) {
         if (tid == 0) {
-            sm.tile = atomicAdd(&ctrs->tile_ctr[1], 1u);
+            // the tile and its item; consecutive tiles of a CTA mostly belong to
+            // the same big bin, whose item is then already in shared memory
+            const u32 t0 = atomicAdd(&ctrs->tile_ctr[1], 1u);
+            sm.tile = t0;
             sm.abort = 0;
+            if (t0 < n_tiles) {
+                const u32 idx = tile_item[t0];
+                if (idx != sm.item_idx) {
+                    sm.item = items[idx];
+                    sm.item_idx = idx;
+                }
+            }
         }
         __syncthreads();
         const u32 t = sm.tile;
         if (t >= n_tiles)
             break;
-        const WorkItem item = items[tile_item[t]];
+        const WorkItem item = sm.item;
         const u32 j = t - item.tile_base;
         const u64 lo = item.begin + (u64)j * TILE;
         const u32 m = (u32)min((u64)TILE, item.begin + item.count - lo);
