@@ -43,6 +43,23 @@ import numpy as np  # noqa: E402
 import datagen  # noqa: E402
 
 METRIC = "sorted records/s and % HBM peak at 1 GB300; plain vs learned/batched, bit-exact"
+
+
+def job_time_ms(local_ms: float, dist=None, device: str = "cuda") -> float:
+    """Whole-job time of a timed region: the slowest rank's own time (every
+    rank timed the same steps between barriers)."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(records_per_rank: int, world: int, steps: int, job_ms: float) -> float:
+    """Whole-job throughput: the records every rank sorted over the job time."""
+    return records_per_rank * world * steps / (job_ms / 1e3)
+
 UNIT = "records/s"
 
 WORKLOADS = {
@@ -386,12 +403,8 @@ def main():
     if pkg.raduls_stream_status() != 0:
         raise SystemExit("device-side error during the timed steps")
 
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = n * world * args.steps / (tot_ms / 1e3)
+    tot_ms = job_time_ms(sum(step_ms), dist)
+    value = job_rate(n, world, args.steps, tot_ms)
 
     # the same input through the plain path (learned workloads) or a per-array
     # plain loop over a prefix of the arrays (batched workload), for comparison
@@ -464,12 +477,8 @@ def main():
             torch.cuda.synchronize()
             barrier()
             e2e_ms.append(ev0.elapsed_time(ev1))
-        et = sum(e2e_ms)
-        if dist is not None:
-            t = torch.tensor([et], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": n * world * args.e2e_steps / (et / 1e3), "unit": UNIT,
+        et = job_time_ms(sum(e2e_ms), dist)
+        e2e = {"value": job_rate(n, world, args.e2e_steps, et), "unit": UNIT,
                "h2d_bytes_per_step": n * rec, "d2h_bytes_per_step": n * rec,
                "ms_per_step": et / args.e2e_steps, "ms_steps": [round(x, 2) for x in e2e_ms]}
         del host_out
