@@ -228,6 +228,7 @@ scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__re
 
     if (tid == 0)
         sm.item_idx = ~0u;
+    u32 err_seen = 0;  // thread 0: the error word as read when the tile was taken
     for (;;) {
         if (tid == 0) {
             // the tile and its item; consecutive tiles of a CTA mostly belong to
@@ -235,6 +236,7 @@ scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__re
             const u32 t0 = atomicAdd(&ctrs->tile_ctr[1], 1u);
             sm.tile = t0;
             sm.abort = 0;
+            err_seen = ld_relaxed_u32(&ctrs->err);  // read early: the answer is needed only before the writes
             if (t0 < n_tiles) {
                 const u32 idx = tile_item[t0];
                 if (idx != sm.item_idx) {
@@ -306,7 +308,7 @@ scatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__re
         }
         if (tid < RADIX)
             sm.goff[tid] = bases[(u64)item.row * RADIX + tid] + sm.excl[tid] - sm.rank.tstart[tid];
-        if (tid == 0 && ld_relaxed_u32(&ctrs->err) != 0)
+        if (tid == 0 && err_seen != 0)  // another CTA failed: leave the rest of the pass alone
             sm.abort = 1;
         __syncthreads();
         if (!sm.abort) {
