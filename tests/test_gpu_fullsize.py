@@ -40,7 +40,6 @@ def _check(out, pristine, kw: int, iw: int, offsets=None):
     dev = out.device
     sign = -(1 << 63)
     seen = torch.zeros(n, dtype=torch.bool, device=dev)
-    seg_start = None
     if offsets is not None:
         offs = torch.from_numpy(offsets.astype(np.int64)).to(dev)
     for a in range(0, n, CHUNK):
@@ -53,7 +52,7 @@ def _check(out, pristine, kw: int, iw: int, offsets=None):
         if offsets is not None:
             pos = torch.arange(a, b, device=dev)
             s_pos = torch.searchsorted(offs, pos, right=True) - 1
-            s_idx = torch.searchsorted(offs, idx, right=True) - 1
+            s_idx = torch.searchsorted(offs, idx.contiguous(), right=True) - 1
             assert bool((s_pos == s_idx).all()), "a record left its array"
         # order between row i and row i+1 for i in [a, min(b, n-1))
         e = min(b + 1, n)
