@@ -176,45 +176,67 @@ __global__ void lm_warm_kernel(const Model *__restrict__ M, u32 stage, const u64
 
 // ---------------------------------------------------------------- training
 
-// One warp per (stage, segment): softplus of the parameters, running sums ->
-// heights, softplus total; also clears this step's accumulators.
-__global__ void lm_heights_kernel(const Model *__restrict__ M, const float *__restrict__ theta,
-                                  float *__restrict__ h, float *__restrict__ tot, double *__restrict__ E,
-                                  double *__restrict__ G, double *__restrict__ Z, double *__restrict__ loss)
+// Exclusive scan of one value per thread over a 256-thread block; `total`
+// receives the block sum.  wbuf: 8 entries of shared memory.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan256(T v, T &total, T *wbuf)
 {
-    const u32 lane = threadIdx.x & 31u;
-    const u32 wid = blockIdx.x * (blockDim.x / 32u) + (threadIdx.x >> 5);
-    if (wid >= 2u * RADIX)
-        return;
-    const u32 stage = wid / RADIX, j = wid % RADIX;
+    const u32 lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T x = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= (u32)o)
+            incl += x;
+    }
+    if (lane == 31)
+        wbuf[w] = incl;
+    __syncthreads();
+    T before = 0, tot = 0;
+#pragma unroll
+    for (u32 i = 0; i < 8; ++i) {
+        tot += wbuf[i];
+        before += i < w ? wbuf[i] : (T)0;
+    }
+    total = tot;
+    __syncthreads();
+    return before + incl - v;
+}
+
+// One 256-thread block per (stage, segment): softplus of the parameters,
+// running sums -> heights, softplus total; also clears this step's
+// accumulators.  Each thread takes a contiguous run of the segment's
+// parameters, so a segment of thousands of knots costs one block scan.
+__global__ void __launch_bounds__(256)
+lm_heights_kernel(const Model *__restrict__ M, const float *__restrict__ theta, float *__restrict__ h,
+                  float *__restrict__ tot, double *__restrict__ E, double *__restrict__ G, double *__restrict__ Z,
+                  double *__restrict__ loss)
+{
+    __shared__ float wbuf[8];
+    const u32 stage = blockIdx.x / RADIX, j = blockIdx.x % RADIX;
     const ModelSeg sg = M->seg[stage][j];
     const u32 koff = sg.koff, m = sg.m, poff = sg.poff;
-    float total = 0.f;
-    for (u32 l = lane; l < m - 1u; l += 32)
-        total += softplus_f(theta[poff + l]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        total += __shfl_xor_sync(FULL_MASK, total, o);
-    float carry = 0.f;
-    for (u32 base = 0; base < m; base += 32) {
-        const u32 i = base + lane;  // knot i: h_i = sum of increments l < i
-        const float inc = (i >= 1u && i < m) ? softplus_f(theta[poff + i - 1u]) : 0.f;
-        float incl = inc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float v = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= (u32)o)
-                incl += v;
-        }
-        if (i < m)
-            h[koff + i] = (i == m - 1u) ? 1.f : (carry + incl) / total;
-        carry += __shfl_sync(FULL_MASK, incl, 31);
-        if (i < m) {
-            E[koff + i] = 0.0;
-            G[koff + i] = 0.0;
-        }
+    const u32 np = m > 0u ? m - 1u : 0u;  // parameters: one softplus increment per interval
+    const u32 per = (np + 255u) / 256u;
+    const u32 l0 = threadIdx.x * per, l1 = min(np, l0 + per);
+    float part = 0.f;
+    for (u32 l = l0; l < l1; ++l)
+        part += softplus_f(theta[poff + l]);
+    float total;
+    float run = block_excl_scan256<float>(part, total, wbuf);
+    // knot i = l + 1 closes interval l: h_i = (increments of intervals < i) / total
+    if (threadIdx.x == 0 && m > 0u)
+        h[koff] = m == 1u ? 1.f : 0.f;
+    for (u32 l = l0; l < l1; ++l) {
+        run += softplus_f(theta[poff + l]);
+        const u32 i = l + 1u;
+        h[koff + i] = (i == m - 1u) ? 1.f : run / total;
     }
-    if (lane == 0) {
+    for (u32 i = threadIdx.x; i < m; i += 256u) {
+        E[koff + i] = 0.0;
+        G[koff + i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
         tot[stage * RADIX + j] = total;
         if (stage == 0) {
             Z[j] = 0.0;
@@ -314,51 +336,44 @@ __global__ void lm_grad_kernel(const Model *__restrict__ M, const u64 *__restric
     }
 }
 
-// One warp per segment of one stage: gradient of each parameter from the
-// interval sums (suffix sums of E give the [l < i] term) and, unless grad_out
-// is set, an Adam step:
-//   grad_l = 2/S * sigmoid(theta_l) / T_j * (sum_{i>l} E_i + G_l - Z_j).
-__global__ void lm_update_kernel(const Model *__restrict__ M, u32 stage, float *__restrict__ theta,
-                                 float *__restrict__ am, float *__restrict__ av, const float *__restrict__ tot,
-                                 const double *__restrict__ E, const double *__restrict__ G,
-                                 const double *__restrict__ Z, u32 S, float lr, float b1t, float b2t,
-                                 float *__restrict__ grad_out)
+// One 256-thread block per segment of the stage: the gradient of every
+// parameter l, 2 / S / T_j * sigmoid(theta_l) * (sum of E over the intervals
+// above l + G_l - Z_j), then an Adam step (or the raw gradient to grad_out).
+// The suffix sums come from one block scan over contiguous runs of intervals.
+__global__ void __launch_bounds__(256)
+lm_update_kernel(const Model *__restrict__ M, u32 stage, float *__restrict__ theta, float *__restrict__ am,
+                 float *__restrict__ av, const float *__restrict__ tot, const double *__restrict__ E,
+                 const double *__restrict__ G, const double *__restrict__ Z, u32 S, float lr, float b1t, float b2t,
+                 float *__restrict__ grad_out)
 {
-    const u32 lane = threadIdx.x & 31u;
-    const u32 j = blockIdx.x * (blockDim.x / 32u) + (threadIdx.x >> 5);
-    if (j >= (u32)RADIX)
-        return;
+    __shared__ double wbuf[8];
+    const u32 j = blockIdx.x;
     const ModelSeg sg = M->seg[stage][j];
-    const u32 koff = sg.koff, np = sg.m - 1u, poff = sg.poff;
+    const u32 koff = sg.koff, np = sg.m > 0u ? sg.m - 1u : 0u, poff = sg.poff;
     const double zj = Z[j];
     const double scale = 2.0 / (double)S / (double)tot[stage * RADIX + j];
-    double carry = 0.0;
-    for (int top = (int)np - 1; top >= 0; top -= 32) {
-        const int l = top - (int)lane;
-        const double el = (l >= 0) ? E[koff + (u32)l] : 0.0;
-        double incl = el;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double v = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= (u32)o)
-                incl += v;
-        }
-        const double suffix_excl = carry + incl - el;  // sum over the intervals above l
-        carry += __shfl_sync(FULL_MASK, incl, 31);
-        if (l >= 0) {
-            const u32 pi = poff + (u32)l;
-            const float th = theta[pi];
-            const double gsum = suffix_excl + G[koff + (u32)l] - zj;
-            const float grad = (float)(scale * (double)sigmoid_f(th) * gsum);
-            if (grad_out) {
-                grad_out[pi] = grad;
-            } else {
-                const float mo = 0.9f * am[pi] + 0.1f * grad;
-                const float ve = 0.999f * av[pi] + 0.001f * grad * grad;
-                am[pi] = mo;
-                av[pi] = ve;
-                theta[pi] = th - lr * (mo / b1t) / (sqrtf(ve / b2t) + 1e-12f);
-            }
+    const u32 per = (np + 255u) / 256u;
+    const u32 l0 = threadIdx.x * per, l1 = min(np, l0 + per);
+    double part = 0.0;
+    for (u32 l = l0; l < l1; ++l)
+        part += E[koff + l];
+    double total;
+    double upto = block_excl_scan256<double>(part, total, wbuf);  // E over intervals below this run
+    for (u32 l = l0; l < l1; ++l) {
+        upto += E[koff + l];
+        const double above = total - upto;  // E over the intervals above l
+        const u32 pi = poff + l;
+        const float th = theta[pi];
+        const double gsum = above + G[koff + l] - zj;
+        const float grad = (float)(scale * (double)sigmoid_f(th) * gsum);
+        if (grad_out) {
+            grad_out[pi] = grad;
+        } else {
+            const float mo = 0.9f * am[pi] + 0.1f * grad;
+            const float ve = 0.999f * av[pi] + 0.001f * grad * grad;
+            am[pi] = mo;
+            av[pi] = ve;
+            theta[pi] = th - lr * (mo / b1t) / (sqrtf(ve / b2t) + 1e-12f);
         }
     }
 }
@@ -502,13 +517,13 @@ cudaError_t lm_launch_step(const Model *M, u32 stage, float *theta, float *am, f
                            double *E, double *G, double *Z, double *loss, const u64 *sample, const u32 *seg_start,
                            u32 S, float lr, int step, float *grad_out, cudaStream_t st)
 {
-    lm_heights_kernel<<<2 * RADIX / 8, 256, 0, st>>>(M, theta, h, tot, E, G, Z, loss);
+    lm_heights_kernel<<<2 * RADIX, 256, 0, st>>>(M, theta, h, tot, E, G, Z, loss);
     u32 blocks = (S + 255) / 256;
     if (blocks > 2048)
         blocks = 2048;
     lm_grad_kernel<<<blocks ? blocks : 1, 256, 0, st>>>(M, sample, seg_start, S, stage, E, G, Z, loss);
     const float b1t = 1.f - powf(0.9f, (float)step), b2t = 1.f - powf(0.999f, (float)step);
-    lm_update_kernel<<<RADIX / 8, 256, 0, st>>>(M, stage, theta, am, av, tot, E, G, Z, S, lr, b1t, b2t, grad_out);
+    lm_update_kernel<<<RADIX, 256, 0, st>>>(M, stage, theta, am, av, tot, E, G, Z, S, lr, b1t, b2t, grad_out);
     return cudaGetLastError();
 }
 
@@ -522,7 +537,7 @@ cudaError_t lm_launch_warm(const Model *M, u32 stage, const u64 *sample, const u
 cudaError_t lm_launch_heights(const Model *M, const float *theta, float *h, float *tot, double *E, double *G,
                               double *Z, double *loss, cudaStream_t st)
 {
-    lm_heights_kernel<<<2 * RADIX / 8, 256, 0, st>>>(M, theta, h, tot, E, G, Z, loss);
+    lm_heights_kernel<<<2 * RADIX, 256, 0, st>>>(M, theta, h, tot, E, G, Z, loss);
     return cudaGetLastError();
 }
 
