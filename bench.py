@@ -95,6 +95,43 @@ CLASS_KERNEL = {"scatter": "scatter_kernel (MSD distribution pass of big bins)",
                 "hist": "hist_kernel (digit histograms of big bins)"}
 
 
+def roofline_of(kernel_ms: dict, cls_bytes: dict, cls_launches: dict, steps: int, rec: int, hbm_peak: float,
+                peak_kind: str, total_bytes: int, tot_ms: float, world: int) -> dict:
+    """The JSON line's roofline object from the library's per-class figures
+    summed over the timed steps: per class, algorithmic bytes (read + write
+    of every record it moves) over its CUDA-event time; the dominant class
+    (most time per step) is the roofline's kernel, its `traffic` the ncu DRAM
+    bytes per record moved (DRAM_BYTES_PER_RECORD) times the records a launch
+    moves."""
+    per_kernel = {}
+    for c in CLASS_BYTES:
+        ms = kernel_ms.get(c, 0.0)
+        if ms > 0 and cls_launches.get(c, 0) > 0:
+            gbs = cls_bytes[c] / (ms / 1e3) / 1e9
+            per_kernel[c] = {"ms_per_step": ms / steps, "launches_per_step": cls_launches[c] / steps,
+                             "gbs": gbs, "frac": gbs / hbm_peak}
+    dom = max(per_kernel, key=lambda c: per_kernel[c]["ms_per_step"]) if per_kernel else "scatter"
+    dom_ms, dom_launches, dom_bytes = kernel_ms.get(dom, 0.0), cls_launches.get(dom, 0), cls_bytes.get(dom, 0)
+    achieved = (dom_bytes / (dom_ms / 1e3)) / 1e9 if dom_ms > 0 else None
+    traffic = None
+    if dom in DRAM_BYTES_PER_RECORD and dom_launches and dom != "hist":
+        traffic = DRAM_BYTES_PER_RECORD[dom] * (dom_bytes / (2 * rec)) / dom_launches
+    whole = total_bytes / (tot_ms / 1e3) / 1e9 / world if tot_ms else None
+    return {
+        "bound": "hbm", "kernel": CLASS_KERNEL[dom],
+        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        "frac": (achieved / hbm_peak) if achieved else None,
+        "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+        "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
+        "launch_ms_avg": dom_ms / max(dom_launches, 1),
+        "per_kernel": per_kernel,
+        "whole_sort_gbs": whole,
+        "whole_sort_frac": whole / hbm_peak if whole else None,
+        "kernel_ms_per_step": {k: v / steps for k, v in kernel_ms.items() if v > 0},
+    }
+
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -494,33 +531,8 @@ def main():
                "h2d_bytes_per_step": n * rec, "d2h_bytes_per_step": n * rec,
                "ms_per_step": et / args.e2e_steps, "ms_steps": [round(x, 2) for x in e2e_ms]}
 
-    # per kernel class: algorithmic bytes over its CUDA-event time; the
-    # dominant class (most time per step) is the roofline's kernel
-    per_kernel = {}
-    for c in CLASS_BYTES:
-        ms = kernel_ms.get(c, 0.0)
-        if ms > 0 and cls_launches[c] > 0:
-            gbs = cls_bytes[c] / (ms / 1e3) / 1e9
-            per_kernel[c] = {"ms_per_step": ms / args.steps, "launches_per_step": cls_launches[c] / args.steps,
-                             "gbs": gbs, "frac": gbs / hbm_peak}
-    dom = max(per_kernel, key=lambda c: per_kernel[c]["ms_per_step"]) if per_kernel else "scatter"
-    dom_ms, dom_launches, dom_bytes = kernel_ms.get(dom, 0.0), cls_launches[dom], cls_bytes[dom]
-    achieved = (dom_bytes / (dom_ms / 1e3)) / 1e9 if dom_ms > 0 else None
-    traffic = None
-    if dom in DRAM_BYTES_PER_RECORD and dom_launches and dom != "hist":
-        traffic = DRAM_BYTES_PER_RECORD[dom] * (dom_bytes / (2 * rec)) / dom_launches
-    roofline = {
-        "bound": "hbm", "kernel": CLASS_KERNEL[dom],
-        "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (achieved / hbm_peak) if achieved else None,
-        "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-        "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
-        "launch_ms_avg": dom_ms / max(dom_launches, 1),
-        "per_kernel": per_kernel,
-        "whole_sort_gbs": total_bytes / (tot_ms / 1e3) / 1e9 / world if tot_ms else None,
-        "whole_sort_frac": (total_bytes / (tot_ms / 1e3) / 1e9 / world) / hbm_peak if tot_ms else None,
-        "kernel_ms_per_step": {k: v / args.steps for k, v in kernel_ms.items() if v > 0},
-    }
+    roofline = roofline_of(kernel_ms, cls_bytes, cls_launches, args.steps, rec, hbm_peak, peak_kind, total_bytes,
+                           tot_ms, world)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "ms_steps": [round(x, 2) for x in step_ms],
