@@ -64,6 +64,17 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.raduls_distribution_pass(16, 4096, 10, 16, 8, 9, None) == 1  # digit out of range
     assert lib.raduls_debug_inject(5, 0) == 1
     assert lib.raduls_set_wait_limit_ns(0) == 1
+    # the host entry point: the same record rules, plus its own buffer rules
+    assert lib.raduls_sort_host(16, 4096, 10, 12, 8, None, None) == 1   # rec_bytes not a multiple of 8
+    assert lib.raduls_sort_host(None, 4096, 10, 16, 8, None, None) == 1  # no input
+    assert lib.raduls_sort_host(16, None, 10, 16, 8, None, None) == 1   # no output
+    assert lib.raduls_sort_host(16, 32, 10, 16, 8, None, None) == 1     # partly overlapping host ranges
+    assert lib.raduls_sort_host(None, None, 0, 16, 8, None, None) == 0  # nothing to sort
+    from paper_1612_02557_gb300._lib import Opts
+    bad = Opts(7, 0, 0.0, 0, None)
+    assert lib.raduls_sort_host(16, 4096, 10, 16, 8, ctypes.byref(bad), None) == 1  # unknown mode
+    bad = Opts(2, 20, 0.0, 0, None)
+    assert lib.raduls_sort_host(16, 4096, 10, 16, 8, ctypes.byref(bad), None) == 1  # learned buckets > 2^16
 
 
 def test_python_binding_rejects_bad_modes(lib):
