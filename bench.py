@@ -240,9 +240,10 @@ def _oracle_run(oracle, recs, offs, key, cores):
 
 
 def cpu_baseline(name: str, budget_s: float = 15.0) -> dict:
-    """The oracle, as it stands, on a bounded prefix of the workload (whole
-    records sorted by the LSD counting sort; for the batched workload the
-    prefix's arrays sorted one by one)."""
+    """The oracle, as it stands, on a bounded sample of the workload (a prefix
+    for the uniform and batched workloads, a smaller draw of the same law for
+    the mixtures; whole records sorted by the LSD counting sort; for the
+    batched workload the sample's arrays sorted one by one)."""
     import oracle
     w = WORKLOADS[name]
     cores = oracle.usable_cores()
@@ -259,9 +260,10 @@ def cpu_baseline(name: str, budget_s: float = 15.0) -> dict:
         _oracle_run(oracle, recs, offs, w["key"], cores)
         dt = time.perf_counter() - t0
     m = recs.shape[0]
+    what = (f"first {m} records of the {name} workload" if name in ("uniform8", "uniform16", "batched16")
+            else f"{m} records drawn from the {name} workload's law and seed")
     return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {m} records of the {name} workload ({w['rec']} B records), one LSD oracle sort "
-                      f"with {cores} threads, {dt:.2f} s"}
+            "sample": f"{what} ({w['rec']} B records), one LSD oracle sort with {cores} threads, {dt:.2f} s"}
 
 
 def run_reference(args, rank: int, world: int) -> None:

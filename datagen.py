@@ -13,8 +13,12 @@ shape ``(n, rec_bytes // 8)``.
 
 Random streams: every workload uses numpy ``Generator(PCG64(seed))``.  Large
 arrays are drawn in fixed chunks of ``CHUNK`` records, chunk ``c`` coming from
-``PCG64(seed).jumped(c)``, so the first ``m`` records of a workload do not
-depend on ``n`` and small test inputs are prefixes of the full-size ones.
+``PCG64(seed).jumped(c)``.  For the uniform workloads (and the batched one's
+records) each chunk's draws are sequential, so the first ``m`` records do not
+depend on ``n``: small inputs are prefixes of the full-size ones.  The
+mixtures (``skewed16``, ``widekey32``) draw each chunk's components in
+batches whose size depends on how much of the chunk is filled, so a smaller
+input is a draw of the same law and seed, not a prefix.
 
 Workloads (sizes are the full ones; tests pass a smaller ``n``):
 
