@@ -247,7 +247,7 @@ def cpu_baseline(name: str, budget_s: float = 15.0) -> dict:
     import oracle
     w = WORKLOADS[name]
     cores = oracle.usable_cores()
-    m = 1 << 22
+    m = min(1 << 22, w["n"] or (1 << 22))  # never more than the workload itself
     recs, offs = _prefix(name, m)
     t0 = time.perf_counter()
     _oracle_run(oracle, recs, offs, w["key"], cores)
