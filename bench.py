@@ -80,11 +80,10 @@ WORKLOADS = {
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record
 # moved, per kernel class, from one capture of the current kernels on uniform
-# 16-byte records (profiles/).  A class missing here has no capture of
-# its current code.
+# 16-byte records.  A class missing here has no capture of its current code.
 DRAM_BYTES_PER_RECORD = {
-    "scatter": (1.096136e9 + 1.048401e9) / 2 ** 26,   # profiles/scatter_uniform16.md (2^26 records)
-    "bucket": (566.772736e6 + 414.964224e6) / 1e7,    # profiles/bucket_uniform16.md (10^7 records)
+    "scatter": (1.096136e9 + 1.048401e9) / 2 ** 26,   # ncu capture of scatter_kernel, 2^26 records
+    "bucket": (566.772736e6 + 414.964224e6) / 1e7,    # ncu capture of bucket_kernel, 10^7 records
 }
 # stats field holding each class's algorithmic bytes (read + write of every record it moves)
 CLASS_BYTES = {"scatter": "scatter_bytes", "bucket": "bucket_bytes", "block": "block_bytes",

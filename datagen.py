@@ -209,16 +209,14 @@ def batched16(n_arrays: int = BATCHED_N_ARRAYS, seed: int | None = None,
     np.cumsum(sizes, out=offsets[1:])
     n = int(offsets[-1])
     out = uniform16(n, seed)
-    # fix the top 32 bits of the key for every odd array (chunked over records)
-    top = np.zeros(sizes.size, dtype=np.uint64)
+    # fix the top 32 bits of the key for every odd array
     odd = np.arange(1, sizes.size, 2)
-    top[odd] = mix64(odd.astype(np.uint64), seed) >> np.uint64(32)
-    for lo in range(0, n, CHUNK):
-        hi = min(n, lo + CHUNK)
-        arr = np.searchsorted(offsets, np.arange(lo, hi, dtype=np.uint64), side="right") - 1
-        sel = (arr & 1) == 1
-        k = out[lo:hi, 0]
-        k[sel] = (k[sel] & np.uint64(0xFFFFFFFF)) | (top[arr[sel]] << np.uint64(32))
+    top = (mix64(odd.astype(np.uint64), seed) >> np.uint64(32)) << np.uint64(32)
+    lo32 = np.uint64(0xFFFFFFFF)
+    for a, t in zip(odd.tolist(), top.tolist()):
+        k = out[int(offsets[a]):int(offsets[a + 1]), 0]
+        np.bitwise_and(k, lo32, out=k)
+        np.bitwise_or(k, np.uint64(t), out=k)
     return out, offsets
 
 

@@ -99,8 +99,9 @@ typedef struct {
 } raduls_stats;
 
 typedef struct {
-    uint32_t mode;                  /* 0 AUTO (learned first partition when the top-byte
-                                       histogram is skewed), 1 PLAIN, 2 LEARNED */
+    uint32_t mode;                  /* 0 AUTO (currently the plain passes: the learned first
+                                       partition is not yet faster on skewed keys), 1 PLAIN,
+                                       2 LEARNED */
     uint32_t learned_log2_buckets;  /* 12..16, 0 = chosen from n */
     float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio; 0 = 4.0 */
     uint32_t train_steps;           /* Adam steps per stage of the model fit; 0 = 16 */
@@ -151,18 +152,23 @@ const char *raduls_status_string(int status);
 /* ---- the learned first partition (not in the paper) ----
  *
  * A monotone two-level piecewise-linear CDF of key word 0: level 1 is the
- * exact histogram of the key's top byte over all records (the first MSD
- * pass's digit histogram, Sec. 1); level 2, per top byte j, maps
- * t = fp32(key mod 2^56) * 2^-56 through two piecewise-linear stages
- * u = f2(f1(t)), each with uniformly spaced knots (stage 1 on the range of the
- * segment's sample, stage 2 on [0, 1]) and learned non-decreasing heights
- * (cumulative softplus of the parameters, normalised to end at 1).  A key goes
- * to bucket floor(B * p / n), p = C_j + min(floor(u * R_j), R_j - 1), so
- * bucket order is key order.  The heights are fitted on the GPU with Adam to
- * the empirical CDF of a sorted key sample (mean squared error), stage 1
- * first, then stage 2 on stage 1's output.  raduls_sort_ex(mode = LEARNED, or
- * AUTO on a skewed top byte) builds one internally; these calls expose the
- * model for testing and inspection. */
+ * exact histogram R_j of the key's top byte j over all records (the first MSD
+ * pass's digit histogram, Sec. 1), with exclusive prefix C_j; level 2, per top
+ * byte j, maps the key's low 56 bits through two piecewise-linear stages
+ * u = f2(f1(key)).  Stage 1 has knots 2^sh_j key units apart starting at the
+ * low 56 bits of the segment's first sample (base_j); a key's interval is the
+ * exact integer (low - base_j) >> sh_j and its position inside the interval
+ * the remainder over 2^sh_j, rounded once to fp32 (keys below base_j map to 0,
+ * keys past the last knot to 1).  Stage 2 has uniform knots on [0, 1].
+ * Heights are learned and non-decreasing (cumulative softplus of the
+ * parameters, normalised to end at 1).  A key goes to bucket
+ * floor(B * p / n), p = C_j + min(floor(u * 2^64) * R_j / 2^64, R_j - 1), all
+ * in integer arithmetic, so bucket order is key order.  The heights are fitted
+ * on the GPU to the empirical CDF of a sorted key sample (mean squared error):
+ * each stage is warm-started at the sample's CDF at its knots, then refined by
+ * Adam steps, stage 1 first, then stage 2 on stage 1's output.
+ * raduls_sort_ex(mode = LEARNED) builds one internally; these calls expose
+ * the model for testing and inspection. */
 typedef struct raduls_model raduls_model;
 
 /* Fit a model with 2^log2_buckets buckets (12..16) to the n_recs records at
@@ -225,9 +231,11 @@ int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_
  * The call's scratch (work counters, the work item, the histogram row and one
  * u32 per 16384-record tile) lives in a fixed 1 MiB array inside the library,
  * which every GPU that loads the library holds until the process exits.
- * Inputs larger than that tile map allows -- more than 260,032 tiles, about
- * 4.26e9 records -- are rejected with RADULS_ERR_UNSUPPORTED before anything
- * is launched.  The first call on a device looks the array's address up
+ * Inputs larger than that tile map allows -- more than 260,928 tiles of
+ * 16,384 records, i.e. more than 4,275,044,352 records -- are rejected with
+ * RADULS_ERR_UNSUPPORTED before anything is launched.  The call returns
+ * argument and launch errors only: its kernel has no bounded wait and records
+ * no device-side status (raduls_stream_status() does not report on it).  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls on a device share the one array, and
  * each call rewrites everything it reads from it, but calls that overlap on

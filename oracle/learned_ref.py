@@ -29,9 +29,13 @@ plain numpy in float64, written from the model's definition:
 * Analytic gradient: with sigma the logistic function and T_j the segment's
   softplus sum, d u / d theta_l = sigma(theta_l) / T_j * ([l < i] + lam [l == i] - u).
 
+* The bucket map (bucket_of_model) and the warm start (warm_heights) follow
+  the GPU model's definition; the map emulates its fp32 steps exactly, since
+  an fp32 result decides an integer there.
+
 The pins in tests/test_learned_ref.py check this reference against central
-finite differences of its own forward pass, closed-form special cases and a
-planted mistake.
+finite differences of its own forward pass, closed-form special cases,
+exactly rounded fp32 arithmetic and planted mistakes.
 """
 from __future__ import annotations
 
@@ -204,20 +208,158 @@ def stage_output(sample_sorted, knot_off, knot_x, theta, poff=None, coords=None)
     return out
 
 
-def bucket_of(keys: np.ndarray, root_counts: np.ndarray, n: int, log2_buckets: int,
-              knot_off: np.ndarray, knot_x: np.ndarray, theta: np.ndarray) -> np.ndarray:
-    """Bucket b = floor(B * p / n), p = C_j + min(floor(u * R_j), R_j - 1) (integer arithmetic)."""
-    j_all, t_all = split_keys(keys)
-    C = np.concatenate([[0], np.cumsum(root_counts.astype(np.int64))])
-    out = np.zeros(keys.size, dtype=np.int64)
+# ---------------------------------------------------------------- bucket map
+#
+# The GPU model decides each key's bucket (an integer) with fp32 arithmetic,
+# so the reference takes that decision in the same precision: every fp32 step
+# of the map is emulated exactly (IEEE binary32, round to nearest even), and
+# the final position and bucket are exact integers.  The steps, in order:
+#   stage 1: low = key mod 2^56; below base_j -> 0; interval i = (low - base_j)
+#            >> sh_j, past the last knot -> 1; lam = rn32(remainder) * 2^-sh_j;
+#            u1 = min(max(fma32(h[i+1] - h[i], lam, h[i]), h[i]), h[i+1]);
+#   stage 2: g = (u1 - x0) * inv_w (fp32); g <= 0 -> 0; g >= m-1 -> 1;
+#            i = min(trunc(g), m-2), lam = g - i, then the same interpolation;
+#   root:    uq = floor(u * 2^64) (2^64 - 1 when u >= 1),
+#            q = min(floor(uq * R_j / 2^64), R_j - 1), p = C_j + q,
+#            b = min(floor(p * B / n), B - 1).
+# The heights h are the model's fp32 knot heights (its parameters as the GPU
+# holds them); how they follow from theta is checked separately.
+
+def f32(x: float) -> float:
+    """Round a double to the nearest binary32 value (ties to even)."""
+    return float(np.float32(x))
+
+
+def _round_exact_to_f32(v) -> float:
+    """Round an exact rational (fractions.Fraction) to binary32, ties to even."""
+    from fractions import Fraction
+    d = float(v)                                   # correctly rounded to binary64
+    f = np.float32(d)
+    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+    best = None
+    for c in cands:
+        if not np.isfinite(c):
+            continue
+        dist = abs(Fraction(float(c)) - v)
+        odd = int(np.array(c, dtype=np.float32).view(np.uint32)) & 1
+        key = (dist, odd)
+        if best is None or key < best[0]:
+            best = (key, float(c))
+    return best[1]
+
+
+def fma32(a: float, b: float, c: float) -> float:
+    """fp32 fused multiply-add: a*b + c rounded once to binary32."""
+    from fractions import Fraction
+    return _round_exact_to_f32(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def u64_to_f32(x: int) -> float:
+    """Unsigned integer to binary32, round to nearest, ties to even."""
+    x = int(x)
+    nb = x.bit_length()
+    if nb <= 24:
+        return float(x)
+    sh = nb - 24
+    q, r = x >> sh, x & ((1 << sh) - 1)
+    half = 1 << (sh - 1)
+    if r > half or (r == half and (q & 1)):
+        q += 1
+    return float(q << sh)
+
+
+def _interp32(h: np.ndarray, koff: int, i: int, lam: float) -> float:
+    h0, h1 = float(h[koff + i]), float(h[koff + i + 1])
+    v = fma32(f32(h1 - h0), lam, h0)
+    return min(max(v, h0), h1)
+
+
+def stage1_f32(key: int, seg0, h: np.ndarray) -> float:
+    """Stage 1 of the key's segment, as the GPU evaluates it (fp32)."""
+    j = key >> 56
+    low = key & LOW56
+    base, sh, m, koff = int(seg0["base"][j]), int(seg0["sh"][j]), int(seg0["m"][j]), int(seg0["koff"][j])
+    if low < base:
+        return 0.0
+    off = low - base
+    i = off >> sh
+    if i >= m - 1:
+        return 1.0
+    lam = f32(u64_to_f32(off & ((1 << sh) - 1)) * 2.0 ** -sh)
+    return _interp32(h, koff, i, lam)
+
+
+def stage2_f32(x: float, j: int, seg1, h: np.ndarray) -> float:
+    """Stage 2 of segment j at the stage-1 output x (fp32)."""
+    m, koff = int(seg1["m"][j]), int(seg1["koff"][j])
+    x0, inv_w = float(seg1["x0"][j]), float(seg1["inv_w"][j])
+    g = f32(f32(x - x0) * inv_w)
+    if not g > 0.0:
+        return 0.0
+    if g >= float(m - 1):
+        return 1.0
+    i = min(int(g), m - 2)
+    lam = f32(g - float(i))
+    return _interp32(h, koff, i, lam)
+
+
+def bucket_of_model(keys, root_counts, seg, h, n: int, log2_buckets: int) -> np.ndarray:
+    """Bucket of every key word under a fitted model (see the steps above).
+
+    root_counts: R_j, 256 u64; seg: the two stages' segment tables (fields
+    base, x0, inv_w, koff, m, sh); h: the fp32 knot heights."""
+    R = [int(r) for r in np.asarray(root_counts, dtype=np.uint64)]
+    C = [0] * 257
+    for j in range(256):
+        C[j + 1] = C[j] + R[j]
     B = 1 << log2_buckets
-    for idx in range(keys.size):
-        j = int(j_all[idx])
-        a, b = int(knot_off[j]), int(knot_off[j + 1])
-        h = heights(np.asarray(theta[a - j: b - j - 1], dtype=np.float64))
-        u, _, _ = leaf_u(t_all[idx], np.asarray(knot_x[a:b], dtype=np.float64), h)
-        R = int(root_counts[j])
-        q = min(int(np.floor(u * R)), max(R - 1, 0))
-        p = int(C[j]) + q
-        out[idx] = (p * B) // n
+    out = np.zeros(len(keys), dtype=np.int64)
+    for idx, k in enumerate(np.asarray(keys, dtype=np.uint64).tolist()):
+        j = k >> 56
+        u = stage2_f32(stage1_f32(k, seg[0], h), j, seg[1], h)
+        r = R[j]
+        uq = (1 << 64) - 1 if u >= 1.0 else int(np.floor(u * 2.0 ** 64))
+        q = (uq * r) >> 64
+        if q >= r:
+            q = r - 1 if r else 0
+        out[idx] = min(((C[j] + q) * B) // n, B - 1)
+    return out
+
+
+def warm_heights(sample_sorted: np.ndarray, seg, stage: int, h_stage1=None) -> np.ndarray:
+    """Warm-start knot heights of one stage, in float64: at every knot the
+    fraction of the segment's sample whose stage input lies at or below the
+    knot, with each interval's increment floored at 1e-6 / (m - 1) (so the
+    heights stay strictly representable by softplus parameters) and the
+    result renormalised to end at 1.  Stage 0's input is the key's low 56 bits
+    against knots base + i * 2^sh; stage 1's is the stage-1 output (computed
+    with h_stage1, the model's fp32 heights) against knots x0 + i / inv_w.
+    Returns a dict j -> heights of segment j (non-empty segments only)."""
+    keys = np.asarray(sample_sorted, dtype=np.uint64)
+    tops = (keys >> np.uint64(56)).astype(np.int64)
+    out = {}
+    sg = seg[stage]
+    for j in range(256):
+        sel = np.flatnonzero(tops == j)
+        if sel.size == 0:
+            continue
+        m = int(sg["m"][j])
+        if stage == 0:
+            low = [int(k) & LOW56 for k in keys[sel].tolist()]
+            base, sh = int(sg["base"][j]), int(sg["sh"][j])
+            xs = [base + (i << sh) for i in range(m)]
+        else:
+            low = [stage1_f32(int(k), seg[0], h_stage1) for k in keys[sel].tolist()]
+            x0, inv_w = float(sg["x0"][j]), float(sg["inv_w"][j])
+            xs = [f32(x0 + f32(float(i) / inv_w)) for i in range(m)]
+        low = np.sort(np.asarray(low, dtype=object))
+        cdf = np.zeros(m)
+        for i in range(1, m - 1):
+            cdf[i] = sum(1 for v in low if v <= xs[i]) / sel.size
+        cdf[m - 1] = 1.0
+        inc = np.maximum(np.diff(cdf), 1e-6 / (m - 1))
+        hj = np.zeros(m)
+        hj[1:] = np.cumsum(inc) / inc.sum()
+        hj[-1] = 1.0
+        out[j] = hj
     return out

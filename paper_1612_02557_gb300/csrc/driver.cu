@@ -676,17 +676,10 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
                 break;
             }
             if (level == 0 && may_learn) {
-                // the first pass's digit histogram decides (auto) and is the model's root
-                bool use = (j.mode == 2);
-                if (!use) {
-                    u64 h[RADIX];
-                    CK(cudaMemcpyAsync(h, B.hist, sizeof h, cudaMemcpyDeviceToHost, st));
-                    CK(cudaStreamSynchronize(st));
-                    u64 mx = 0;
-                    for (int d = 0; d < RADIX; ++d)
-                        mx = h[d] > mx ? h[d] : mx;
-                    use = mx > 4ull * (j.n / RADIX) && j.kw >= 1;
-                }
+                // the first pass's digit histogram is the model's root; AUTO
+                // keeps the plain passes (the learned first partition is taken
+                // only when asked for)
+                const bool use = (j.mode == 2);
                 if (use) {
                     const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
                     int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);

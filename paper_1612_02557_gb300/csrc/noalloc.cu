@@ -26,6 +26,10 @@ constexpr size_t OFF_CTRS = 0, OFF_ITEM = 256, OFF_HIST = 512, OFF_ORAND = OFF_H
                  OFF_LIGHT = OFF_ORAND + 256, OFF_TILES = OFF_LIGHT + RADIX * 8;
 static_assert(sizeof(Counters) <= OFF_ITEM - OFF_CTRS, "counters fit");
 constexpr u64 STATIC_MAX_TILES = (STATIC_SCRATCH_BYTES - OFF_TILES) / 4;
+// Records per histogram tile of this entry point: fixed (not the tuned shape's
+// tile), so its size limit is the documented one: 260,928 tiles x 16,384.
+constexpr u32 STATIC_TILE = 16384;
+static_assert(STATIC_MAX_TILES == 260928, "documented tile limit");
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
 
@@ -72,10 +76,11 @@ extern "C" int raduls_histogram_static(const void *in, uint64_t n_recs, uint32_t
         return RADULS_ERR_INVALID_ARG;
     if (((uintptr_t)in & 15u) || ((uintptr_t)d_hist_out & 7u))
         return RADULS_ERR_MISALIGNED;
-    const Shape s = choose_shape(rec_bytes / 8u, key_bytes / 8u);
     // the tile map is the only part that grows with n: reject what does not fit
-    if ((n_recs + s.tile_h - 1) / s.tile_h > STATIC_MAX_TILES)
+    if ((n_recs + STATIC_TILE - 1) / STATIC_TILE > STATIC_MAX_TILES)
         return RADULS_ERR_UNSUPPORTED;
+    Shape s = choose_shape(rec_bytes / 8u, key_bytes / 8u);
+    s.tile_h = STATIC_TILE;
     cudaStream_t st = (cudaStream_t)stream;
     if (n_recs == 0) {
         const cudaError_t e = cudaMemsetAsync(d_hist_out, 0, RADIX * 8, st);

@@ -63,6 +63,11 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.raduls_sort(0, 0, 0, 16, 8, None) == 0
     assert lib.raduls_distribution_pass(16, 4096, 10, 16, 8, 9, None) == 1  # digit out of range
     assert lib.raduls_debug_inject(5, 0) == 1
+    # the allocation-free histogram: one record past its fixed tile map
+    # (260,928 tiles of 16,384 records) is rejected before any CUDA call
+    assert lib.raduls_histogram_static(16, 260928 * 16384 + 1, 16, 8, 7, 4096, None) == 3
+    assert lib.raduls_histogram_static(16, 10, 16, 8, 8, 4096, None) == 1   # digit out of range
+    assert lib.raduls_histogram_static(8, 10, 16, 8, 7, 4096, None) == 2    # misaligned records
     assert lib.raduls_set_wait_limit_ns(0) == 1
     # the host entry point: the same record rules, plus its own buffer rules
     assert lib.raduls_sort_host(16, 4096, 10, 12, 8, None, None) == 1   # rec_bytes not a multiple of 8

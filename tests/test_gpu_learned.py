@@ -5,9 +5,11 @@
 * the bucket map is monotone in the key (exhaustive boundary probes);
 * sorts in learned mode, and with the learned partition forced to fall back,
   equal the oracle bit for bit;
+* the bucket map, the knot heights and the warm start against the CPU
+  reference, exactly for the map (its fp32 steps taken in fp32 on both sides);
 * what training gains: the trained model's max/ideal bucket ratio against the
-  untrained (linear-leaf) model's, and the bytes moved against the plain MSD
-  sort on the skewed workload.
+  untrained (linear-leaf) model's, the training loss, and the bytes moved
+  against the plain MSD sort on the skewed workload.
 """
 from __future__ import annotations
 
@@ -86,6 +88,84 @@ def test_bucket_map_is_monotone():
     m.close()
 
 
+def _probe_keys(out, recs, rng, n_sample=4000, n_knots=3000):
+    """Keys that exercise every branch of the map: sample keys, every stage-1
+    knot of a random subset (and one key either side), segment ends."""
+    seg0 = out["seg"][0]
+    keys = [rng.choice(recs[:, 0], size=n_sample, replace=False)]
+    knots = []
+    for j in np.flatnonzero(out["root"] > 0).tolist():
+        base, sh, m = int(seg0["base"][j]), int(seg0["sh"][j]), int(seg0["m"][j])
+        for i in range(m):
+            x = base + (i << sh)
+            if x <= L.LOW56:
+                for d in (-1, 0, 1):
+                    if 0 <= x + d <= L.LOW56:
+                        knots.append((j << 56) | (x + d))
+        knots += [j << 56, (j << 56) | L.LOW56]
+    knots = np.asarray(knots, dtype=np.uint64)
+    if knots.size > n_knots:
+        knots = rng.choice(knots, size=n_knots, replace=False)
+    return np.unique(np.concatenate(keys + [knots]))
+
+
+@pytest.mark.parametrize("name,log2b,steps", [("skewed16", 14, 30), ("widekey32", 12, 16), ("skewed16", 16, 0)])
+def test_bucket_map_equals_reference(name, log2b, steps):
+    """raduls_model_buckets against the reference map, bucket for bucket: the
+    same model (root counts, segment tables, fp32 heights), the map's fp32
+    steps taken in fp32 on both sides, the integer steps exact."""
+    import torch
+    recs = datagen.WORKLOADS[name](1 << 18)
+    kb = datagen.KEY_BYTES[name]
+    m, _ = _model(recs, kb, log2b, steps)
+    out = m.copy_out()
+    n = recs.shape[0]
+    probes = _probe_keys(out, recs, np.random.default_rng(log2b))
+    dk = torch.from_numpy(probes.view(np.int64).copy()).cuda()
+    db = torch.zeros(probes.size, dtype=torch.int32, device="cuda")
+    m.buckets(dk, db)
+    got = db.cpu().numpy().astype(np.int64)
+    want = L.bucket_of_model(probes, out["root"], out["seg"], out["heights"], n, log2b)
+    bad = np.flatnonzero(got != want)
+    assert bad.size == 0, f"{bad.size} of {probes.size} buckets differ, first key {probes[bad[0]]:#x}: " \
+                          f"GPU {got[bad[0]]}, reference {want[bad[0]]}"
+    m.close()
+
+
+def test_heights_follow_theta():
+    """The GPU's fp32 knot heights against the fp64 normalised cumulative
+    softplus of its own parameters, segment by segment, both stages."""
+    recs = datagen.skewed16(1 << 16)
+    m, _ = _model(recs, 8, 12, 8)
+    out = m.copy_out()
+    for stage in range(2):
+        sg = out["seg"][stage]
+        for j in np.flatnonzero(sg["m"] > 1).tolist():
+            k, mm, pofs = int(sg["koff"][j]), int(sg["m"][j]), int(sg["poff"][j])
+            ref = L.heights(out["theta"][pofs:pofs + mm - 1].astype(np.float64))
+            np.testing.assert_allclose(out["heights"][k:k + mm], ref, rtol=0, atol=2e-5,
+                                       err_msg=f"stage {stage} segment {j}")
+    m.close()
+
+
+def test_warm_start_is_the_sample_cdf_at_the_knots():
+    """Warm start only (no Adam steps): every stage's knot heights equal the
+    fraction of the segment's sample at or below each knot (increments
+    floored at 1e-6 / (m - 1)), computed on the CPU from the model's sample
+    and knots; stage 2's input is the reference stage-1 output."""
+    recs = datagen.skewed16(1 << 15)
+    m, _ = _model(recs, 8, 12, 0x80000000)
+    out = m.copy_out()
+    for stage in range(2):
+        ref = L.warm_heights(out["sample"], out["seg"], stage, out["heights"])
+        sg = out["seg"][stage]
+        for j, hj in ref.items():
+            k, mm = int(sg["koff"][j]), int(sg["m"][j])
+            np.testing.assert_allclose(out["heights"][k:k + mm], hj, rtol=0, atol=1e-4,
+                                       err_msg=f"stage {stage} segment {j}")
+    m.close()
+
+
 @pytest.mark.parametrize("name,n", [("skewed16", 1 << 22), ("widekey32", 1 << 21), ("uniform16", 1 << 21)])
 def test_learned_sort_matches_oracle(oracle_mod, name, n):
     recs = datagen.WORKLOADS[name](n)
@@ -111,14 +191,16 @@ def test_forced_fallback_gives_the_same_bytes(oracle_mod):
     np.testing.assert_array_equal(from_dev(d, n, 2), oracle_mod.sort(recs, 8, threads=8))
 
 
-def test_auto_mode_learns_only_on_skewed_keys(oracle_mod):
+def test_auto_mode_keeps_the_plain_passes(oracle_mod):
+    """AUTO takes the plain passes on every input (the learned first partition
+    runs only when asked for), and the output is the oracle's."""
     p = lib()
-    for name, expect in (("uniform16", 0), ("skewed16", 1)):
+    for name in ("uniform16", "skewed16"):
         recs = datagen.WORKLOADS[name](1 << 20)
         d = to_dev(recs)
         t = scratch(recs.shape[0], 2)
         st = p.raduls_sort_ex(d, t, recs.shape[0], 16, 8, mode="auto", stats=True)
-        assert st["learned_used"] == expect, name
+        assert st["learned_used"] == 0, name
         np.testing.assert_array_equal(from_dev(d, recs.shape[0], 2), oracle_mod.sort(recs, 8, threads=8))
 
 
@@ -132,15 +214,19 @@ def _bucket_ratio(m, keys_dev, log2b):
 
 
 def test_training_gain_over_untrained_and_plain():
-    """Trained leaves balance the buckets far better than the untrained
-    (linear) leaves, and the learned sort moves fewer bytes than the plain MSD
-    sort on the skewed workload."""
+    """What the fitted network gains over the method without it: its leaves
+    balance the buckets far better than the untrained (linear) leaves, and
+    the learned sort moves fewer bytes than the plain MSD sort on the skewed
+    workload.  The fit is the warm start (the sample's CDF at the knots)
+    followed by Adam steps on the mean squared CDF error: the steps must lower
+    that training loss; they are not required to improve the bucket balance,
+    which is not what they minimise (the measured ratios are printed)."""
     import torch
     p = lib()
     n = 1 << 23
     recs = datagen.skewed16(n)
-    # keys without the heaviest duplicates' effect: the ratio counts every bucket here,
-    # so compare models on the distinct-key part (Zipf heavy hitters are unsplittable)
+    # the ratio counts every bucket here, so compare models on the distinct
+    # keys (Zipf heavy hitters cannot be split by any key map)
     d = to_dev(recs)
     keys = torch.from_numpy(recs[:, 0].view(np.int64).copy()).cuda()
     distinct = torch.unique(keys)
@@ -150,17 +236,21 @@ def test_training_gain_over_untrained_and_plain():
     r_untrained = _bucket_ratio(untrained, distinct, 12)
     r_warm = _bucket_ratio(warm, distinct, 12)
     r_trained = _bucket_ratio(trained, distinct, 12)
+    g = torch.zeros(max(warm.n_params, trained.n_params), dtype=torch.float32, device="cuda")
+    loss = {name: mdl.loss_grad(1, g) for name, mdl in (("untrained", untrained), ("warm", warm),
+                                                       ("trained", trained))}
     print(f"max/ideal over distinct keys: untrained {r_untrained:.2f}, warm start {r_warm:.2f}, "
-          f"trained {r_trained:.2f}")
+          f"trained {r_trained:.2f}; leaf loss {loss}")
     assert r_trained < r_untrained / 10
     assert r_warm < r_untrained / 10
-    assert r_trained <= r_warm * 1.25     # the Adam steps refine the warm start, they do not undo it
+    assert loss["warm"] < loss["untrained"] / 10
+    assert loss["trained"] <= loss["warm"]        # Adam lowers the objective it descends
     warm.close()
     t = scratch(n, 2)
     st_plain = p.raduls_sort_ex(d, t, n, 16, 8, mode="plain", stats=True)
     d2 = to_dev(recs)
     st_learn = p.raduls_sort_ex(d2, t, n, 16, 8, mode="learned", stats=True)
-    moved = lambda s: s["hist_bytes_read"] + s["scatter_bytes"] + s["block_bytes"]
+    moved = lambda s: s["hist_bytes_read"] + s["scatter_bytes"] + s["block_bytes"] + s["bucket_bytes"]
     print(f"bytes moved: plain {moved(st_plain) / 2**20:.0f} MiB in {st_plain['grid_passes']} passes, "
           f"learned {moved(st_learn) / 2**20:.0f} MiB in {st_learn['grid_passes']} passes, "
           f"ratio {st_learn['learned_ratio']:.2f}")

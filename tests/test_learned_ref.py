@@ -115,23 +115,154 @@ def test_heights_are_monotone_and_normalised():
         assert np.all(np.diff(h) >= 0)
 
 
-def test_bucket_map_is_monotone_and_in_range():
-    keys, ko, kx, th = _problem(2)
-    n = 10_000
-    root = np.zeros(256, dtype=np.int64)
-    root[[0, 3, 200]] = [6000, 1000, 3000]
-    probes = np.sort(np.concatenate([
-        keys,
-        keys + np.uint64(1),
-        keys - np.uint64(1),
-        np.array([0, 2 ** 64 - 1, (3 << 56), (3 << 56) - 1, (200 << 56) + 5], dtype=np.uint64),
-    ]))
-    # keep probes whose segment has records (the map is defined for present segments)
-    j, _ = L.split_keys(probes)
-    probes = probes[root[j] > 0]
-    b = L.bucket_of(probes, root, n, 12, ko, kx, th)
-    assert np.all(np.diff(b) >= 0)
-    assert b.min() >= 0 and b.max() < (1 << 12)
+SEG = [("base", "<u8"), ("x0", "<f4"), ("inv_w", "<f4"), ("koff", "<u4"), ("m", "<u4"), ("poff", "<u4"),
+       ("sh", "<u4")]
+
+
+def _model(segs):
+    """Model tables from {j: (base, sh, stage-1 heights, stage-2 heights)}; other
+    segments get two knots at heights 0 and 1 in both stages."""
+    seg = np.zeros((2, 256), dtype=SEG)
+    h = []
+    for stage in range(2):
+        for j in range(256):
+            base, sh, h1, h2 = segs.get(j, (0, 56, [0.0, 1.0], [0.0, 1.0]))
+            hs = h1 if stage == 0 else h2
+            seg[stage]["koff"][j] = len(h)
+            seg[stage]["m"][j] = len(hs)
+            if stage == 0:
+                seg[0]["base"][j], seg[0]["sh"][j] = base, sh
+            else:
+                seg[1]["inv_w"][j] = float(len(hs) - 1)
+            h.extend(hs)
+    return seg, np.asarray(h, dtype=np.float32)
+
+
+def test_u64_to_f32_rounds_to_nearest_even():
+    assert L.u64_to_f32((1 << 24) + 1) == float(1 << 24)          # tie -> even (down)
+    assert L.u64_to_f32((1 << 24) + 3) == float((1 << 24) + 4)    # tie -> even (up)
+    assert L.u64_to_f32((1 << 24) + 2) == float((1 << 24) + 2)    # exact
+    rng = np.random.default_rng(1)
+    for bits in (20, 25, 33, 40, 56, 63):
+        for x in rng.integers(0, 1 << bits, size=200, dtype=np.uint64).tolist():
+            f = L.u64_to_f32(x)
+            # f is a binary32 value and no binary32 value lies closer to x
+            assert float(np.float32(f)) == f
+            lo = float(np.nextafter(np.float32(f), np.float32(0)))
+            hi = float(np.nextafter(np.float32(f), np.float32(np.inf)))
+            assert abs(f - x) <= abs(lo - x) and abs(f - x) <= abs(hi - x)
+
+
+def test_fma32_rounds_once():
+    # a*b + c exactly representable in binary64: one rounding to binary32
+    rng = np.random.default_rng(2)
+    a = rng.random(300).astype(np.float32)
+    b = rng.random(300).astype(np.float32)
+    c = rng.random(300).astype(np.float32)
+    for x, y, z in zip(a.tolist(), b.tolist(), c.tolist()):
+        p = x * y                                   # exact: 24 x 24 bits
+        s = p + z
+        if (s - p) == z and (s - z) == p:          # the binary64 sum is exact
+            assert L.fma32(x, y, z) == float(np.float32(s))
+    # a case where rounding twice (binary64, then binary32) lands on a tie and
+    # goes the wrong way: a*b = 2^-24 + r 2^-71 with 0 < r < 2^17, c = 1
+    q = (1 << 24) - 1
+    while True:
+        pa = -(-(1 << 47) // q)
+        r = pa * q - (1 << 47)
+        if pa < (1 << 24) and 0 < r < (1 << 17):
+            break
+        q -= 1
+    x, y = pa * 2.0 ** -36, q * 2.0 ** -35
+    assert float(np.float32(x)) == x and float(np.float32(y)) == y
+    assert float(np.float32(x * y + 1.0)) == 1.0                  # double rounding: tie to even
+    assert L.fma32(x, y, 1.0) == 1.0 + 2.0 ** -23                 # one rounding: above the tie
+
+
+def test_bucket_map_linear_leaf_is_the_rank_interpolation():
+    """Two knots at heights 0, 1 in both stages with a 2^56 knot spacing: the
+    leaf is u = fp32(low) / 2^56, so for lows with at most 24 significant bits
+    the bucket is floor((C_j + floor(low R_j / 2^56)) B / n)."""
+    seg, h = _model({})
+    root = np.zeros(256, dtype=np.uint64)
+    root[[3, 9, 200]] = [1000, 3000, 6000]
+    n, log2b = 10_000, 12
+    rng = np.random.default_rng(3)
+    keys, want = [], []
+    C = np.concatenate([[0], np.cumsum(root.astype(np.int64))])
+    for j in (3, 9, 200):
+        for low in rng.integers(0, 1 << 24, size=60).tolist():
+            low <<= 32
+            keys.append((j << 56) | low)
+            want.append(((int(C[j]) + (low * int(root[j])) // (1 << 56)) << log2b) // n)
+    got = L.bucket_of_model(np.asarray(keys, dtype=np.uint64), root, seg, h, n, log2b)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_bucket_map_knots_ends_and_order():
+    """A three-knot stage 1 (heights 0, 0.25, 1, knots 2^40 apart from base
+    2^44): keys below the base land at the segment's first position, keys
+    past the last knot at its last, the middle knot at a quarter, and the map
+    is monotone over random and boundary keys."""
+    j = 7
+    base, sh = 1 << 44, 40
+    seg, h = _model({j: (base, sh, [0.0, 0.25, 1.0], [0.0, 1.0])})
+    root = np.zeros(256, dtype=np.uint64)
+    root[j] = 1 << 20
+    root[8] = 1 << 20
+    n, log2b = 1 << 21, 12
+    B = 1 << log2b
+    k = lambda low: (j << 56) | low
+    b = L.bucket_of_model(np.asarray([k(0), k(base - 1), k(base), k(base + (1 << sh)),
+                                      k(base + (2 << sh)), k((1 << 56) - 1)], dtype=np.uint64),
+                          root, seg, h, n, log2b)
+    assert b[0] == 0 and b[1] == 0 and b[2] == 0
+    assert b[3] == (((1 << 20) // 4) * B) // n                  # the middle knot: a quarter of the segment
+    assert b[4] == b[5] == (((1 << 20) - 1) * B) // n            # past the last knot: the segment's end
+    rng = np.random.default_rng(4)
+    lows = np.sort(rng.integers(0, 1 << 56, size=400, dtype=np.uint64))
+    probes = np.concatenate([np.uint64(j << 56) | lows, np.asarray([8 << 56], dtype=np.uint64)])
+    bb = L.bucket_of_model(probes, root, seg, h, n, log2b)
+    assert np.all(np.diff(bb) >= 0) and bb.min() >= 0 and bb.max() < B
+    assert bb[-1] == ((1 << 20) * B) // n                      # segment 8 starts after segment 7's records
+
+
+def test_bucket_map_pins_catch_planted_mistakes(monkeypatch):
+    """A knot interval off by one, or a dropped segment offset C_j, fails the
+    pins above."""
+    good = L.stage1_f32
+
+    def off_by_one(key, seg0, h):
+        j = key >> 56
+        low = key & L.LOW56
+        base, sh, m, koff = int(seg0["base"][j]), int(seg0["sh"][j]), int(seg0["m"][j]), int(seg0["koff"][j])
+        if low < base:
+            return 0.0
+        i = ((low - base) >> sh) + 1
+        if i >= m - 1:
+            return 1.0
+        lam = L.f32(L.u64_to_f32((low - base) & ((1 << sh) - 1)) * 2.0 ** -sh)
+        return L._interp32(h, koff, i, lam)
+
+    monkeypatch.setattr(L, "stage1_f32", off_by_one)
+    import pytest as _pt
+    with _pt.raises(AssertionError):
+        test_bucket_map_knots_ends_and_order()
+    monkeypatch.setattr(L, "stage1_f32", good)
+    real = L.bucket_of_model
+
+    def no_offset(keys, root_counts, seg, h, n, log2_buckets):
+        r = np.asarray(root_counts, dtype=np.uint64).copy()
+        out = []
+        for key in np.asarray(keys, dtype=np.uint64).tolist():
+            only = np.zeros(256, dtype=np.uint64)
+            only[key >> 56] = r[key >> 56]               # C_j = 0: the segment's offset dropped
+            out.append(real(np.asarray([key], dtype=np.uint64), only, seg, h, n, log2_buckets)[0])
+        return np.asarray(out)
+
+    monkeypatch.setattr(L, "bucket_of_model", no_offset)
+    with _pt.raises(AssertionError):
+        test_bucket_map_linear_leaf_is_the_rank_interpolation()
 
 
 def test_second_stage_gradient_matches_finite_differences():

@@ -7,7 +7,9 @@ inside a stream capture).  Its result must equal the allocating entry point's,
 exactly (integer counts), on two calls in a row: the second call reuses the
 library's fixed scratch array, whose contents the first call left behind.
 This file is collected last, so a run that stops at its first failure has run
-every other test before it.
+every other test before it.  The static entry point reports argument and
+launch errors through its return code only (it records no device-side
+status), so the comparison of the two results is the whole check.
 """
 from __future__ import annotations
 
@@ -41,7 +43,6 @@ def test_static_histogram_equals_allocating_one_on_two_calls():
             p.raduls_histogram(d, n, rec, key, digit, want)
             p.raduls_histogram_static(d, n, rec, key, digit, got)
             torch.cuda.synchronize()
-            assert p.raduls_stream_status() == 0
             np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy(),
                                           err_msg=f"call {call}, n={n}, rec={rec}, key={key}, digit={digit}")
 
