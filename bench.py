@@ -308,6 +308,140 @@ def check_sorted_gpu(recs, pristine_keys=None) -> bool:
     return ok
 
 
+def _timed(fn, stream):
+    """Device time (ms) of fn() with CUDA events on `stream`."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def _moved(st) -> int:
+    return st["hist_bytes_read"] + st["scatter_bytes"] + st["block_bytes"] + st["bucket_bytes"]
+
+
+def compare_workload(name: str, pkg, steps: int, warmup: int, hbm_peak: float, peak_kind: str) -> dict:
+    """One comparison of the metric's second half on a full-size workload:
+    the learned (skewed16, widekey32) or batched (batched16) form against the
+    plain MSD sort of the same input, each timed with CUDA events, the input
+    restored from a pristine device copy before every step (untimed), the
+    forms run alternately, and their outputs compared byte for byte."""
+    import torch
+    w = WORKLOADS[name]
+    rec, key, mode = w["rec"], w["key"], w["mode"]
+    offsets = None
+    if name == "batched16":
+        host, offsets = datagen.batched16()
+    else:
+        host = getattr(datagen, name)(w["n"])
+    n = host.shape[0]
+    pristine = torch.from_numpy(host.view(np.int64)).cuda()
+    del host
+    recs = torch.empty_like(pristine)
+    tmp = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+    d_off = torch.from_numpy(offsets.view(np.int64)).cuda() if offsets is not None else None
+    n_segs = offsets.size - 1 if offsets is not None else 0
+    if mode == "batched":
+        tuning = pkg.raduls_autotune(recs, tmp, n, rec, key, d_off, n_segs)
+    else:
+        tuning = pkg.raduls_autotune(recs, tmp, n, rec, key)
+    torch.cuda.synchronize()
+
+    def form():
+        if mode == "batched":
+            pkg.raduls_sort_batched(recs, tmp, d_off, n_segs, rec, key)
+            return None
+        return pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode="learned", stats=True)
+
+    def plain():
+        if mode == "batched":
+            # the plain path on every array, one raduls_sort_ex call each
+            for a in range(n_segs):
+                s0, s1 = int(offsets[a]), int(offsets[a + 1])
+                if s1 - s0 > 1:
+                    pkg.raduls_sort_ex(recs[s0:s1], tmp[s0:s1], s1 - s0, rec, key, mode="plain")
+            return None
+        return pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode="plain", stats=True)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for _ in range(warmup):
+        recs.copy_(pristine)
+        form()
+        recs.copy_(pristine)
+        if mode != "batched":
+            plain()
+    torch.cuda.synchronize()
+    if pkg.raduls_stream_status() != 0:
+        raise SystemExit(f"device status during the {name} warm-up")
+    f_ms, p_ms, f_st, p_st = [], [], None, None
+    for i in range(steps):
+        recs.copy_(pristine)
+        ms, f_st = _timed(form, stream)
+        f_ms.append(ms)
+        if mode != "batched":      # alternate the two forms
+            recs.copy_(pristine)
+            ms, p_st = _timed(plain, stream)
+            p_ms.append(ms)
+    # the form's output, then (for the batched form, whose per-array loop is
+    # long, once) the plain output last, left in recs
+    recs.copy_(pristine)
+    form()
+    f_out = recs.clone()
+    recs.copy_(pristine)
+    if mode == "batched":
+        ms, p_st = _timed(plain, stream)
+        p_ms.append(ms)
+    else:
+        plain()
+    clocks = sampler.stop()
+    if pkg.raduls_stream_status() != 0:
+        raise SystemExit(f"device status during the {name} timed steps")
+    identical = bool(torch.equal(f_out, recs))
+    ordered = None
+    if rec == 16 and key == 8 and mode != "batched":
+        ordered = check_sorted_gpu(recs.view(n, 2), pristine.view(n, 2)[:, 0])
+    fm, pm = sum(f_ms) / len(f_ms), sum(p_ms) / len(p_ms)
+    out = {
+        "desc": w["desc"], "n_records": n, "rec_bytes": rec, "key_bytes": key,
+        "form": mode, "ms_per_step": fm, "records_per_s": n / (fm / 1e3),
+        "ms_steps": [round(x, 2) for x in f_ms],
+        "plain_ms_per_step": pm, "plain_records_per_s": n / (pm / 1e3),
+        "plain_ms_steps": [round(x, 2) for x in p_ms],
+        "speedup_over_plain": pm / fm,
+        "identical_output": identical,
+        "clocks": clocks, "tuning": tuning,
+    }
+    if ordered is not None:
+        out["stable_order_checked"] = ordered
+    if mode == "batched":
+        out["n_arrays"] = n_segs
+        out["plain_form"] = f"every one of the {n_segs} arrays sorted by its own raduls_sort_ex call (plain mode)"
+    else:
+        out["plain_form"] = "the same input sorted by raduls_sort_ex in plain mode"
+        out["learned_used"] = f_st["learned_used"]
+        out["learned_fell_back"] = f_st["learned_fell_back"]
+        out["max_over_ideal_bucket"] = f_st["learned_ratio"]
+        out["bytes_moved"] = _moved(f_st)
+        out["plain_bytes_moved"] = _moved(p_st)
+        for tag, st in (("roofline", f_st), ("plain_roofline", p_st)):
+            cls_b = {c: st[f] for c, f in CLASS_BYTES.items()}
+            cls_l = {c: st["kernel_launches"][c] for c in CLASS_BYTES}
+            rf = roofline_of(st["kernel_ms"], cls_b, cls_l, 1, rec, hbm_peak, peak_kind, _moved(st),
+                             sum(st["kernel_ms"].values()), 1)
+            rf["traffic"] = None       # no ncu capture of this workload's launches
+            out[tag] = rf
+    del pristine, recs, tmp, d_off
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,6 +455,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-tune", action="store_true", help="skip raduls_autotune before the warm-up")
+    ap.add_argument("--compare", default="skewed16,widekey32,batched16",
+                    help="workloads timed against the plain sort after the headline (N = 1 only; '' = none)")
+    ap.add_argument("--compare-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -534,6 +671,17 @@ def main():
 
     roofline = roofline_of(kernel_ms, cls_bytes, cls_launches, args.steps, rec, hbm_peak, peak_kind, total_bytes,
                            tot_ms, world)
+
+    # learned / batched forms against the plain sort, on their own full-size
+    # workloads (one GPU only: the headline's buffers are released first)
+    comparisons = None
+    names = [x for x in args.compare.split(",") if x and x != args.workload]
+    if world == 1 and names:
+        del pristine, recs, tmp, host_in
+        torch.cuda.empty_cache()
+        comparisons = {}
+        for nm in names:
+            comparisons[nm] = compare_workload(nm, pkg, max(1, args.compare_steps), 2, hbm_peak, peak_kind)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "ms_steps": [round(x, 2) for x in step_ms],
@@ -552,6 +700,8 @@ def main():
     }
     if comparison is not None:
         line["comparison"] = comparison
+    if comparisons is not None:
+        line["comparisons"] = comparisons
     if learned_info is not None:
         line["learned"] = learned_info
     if rank == 0:
