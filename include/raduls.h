@@ -251,6 +251,8 @@ typedef struct {
     uint32_t bucket_max;       /* largest mid-size bin sorted by one CTA through L2 (0: class off) */
     float    best_ms;          /* sort time of the chosen setting on the tuning input */
     uint32_t candidates;       /* settings timed */
+    uint32_t digit_bits;       /* widest digit of a distribution pass, in bits (8..12) */
+    uint32_t leaf;             /* sub-bin size (records) the digit widths aim at */
 } raduls_tuning;
 
 /* Autotuner of the launch shapes and size-class thresholds (the paper has no

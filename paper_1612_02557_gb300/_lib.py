@@ -253,6 +253,8 @@ class Tuning(ctypes.Structure):
         ("bucket_max", ctypes.c_uint32),
         ("best_ms", ctypes.c_float),
         ("candidates", ctypes.c_uint32),
+        ("digit_bits", ctypes.c_uint32),
+        ("leaf", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:

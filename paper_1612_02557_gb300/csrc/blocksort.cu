@@ -23,6 +23,8 @@ block_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<THREADS, K> &sm = *reinterpret_cast<BlockSmem<THREADS, K> *>(smem_raw);
+    if (cta_failed(ctrs))
+        return;
     const u64 n_items = ctrs->block;
     for (;;) {
         if (threadIdx.x == 0)

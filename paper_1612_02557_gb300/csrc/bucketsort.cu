@@ -24,6 +24,8 @@
 // chunk (the counting split of Sec. 1, with running offsets in shared memory),
 // and its sub-bins are sorted on chip group by group (onchip.cuh); sub-bins
 // too big for shared memory go on to the next level.
+#include <cstdlib>
+
 #include "midsize.cuh"
 
 namespace raduls {
@@ -55,7 +57,6 @@ __device__ __forceinline__ int bucket_code_item(unsigned char *smem_raw, u64 *__
     const u32 p = item.digit;
     const bool from_tmp = (item.flags & ITEM_IN_TMP) != 0;
     const u64 *src = (from_tmp ? tmp : in) + item.begin * rw;
-    u64 *stg = (from_tmp ? in : tmp) + item.begin * rw;  // the bin's range of the other buffer
     u64 *out = in + item.begin * rw;
     if (tid == 0) {
         atomicAdd(&a.ctrs->bucket_bytes, 2ull * n * rw * 8u);
@@ -363,6 +364,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 bucket_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (cta_failed(a.ctrs))
+        return;
     BucketCommon<THREADS> &cm = *reinterpret_cast<BucketCommon<THREADS> *>(smem_raw);
     // the whole list, or one position window of it
     const u32 first = a.bucket_order ? a.bucket_wstart[a.bucket_window] : 0u;
@@ -575,7 +578,7 @@ __device__ __forceinline__ void bucket_split_item(unsigned char *smem_raw, u64 *
         u64 *gout = out + (u64)ga * rw;
         if (c0 <= WARP_MAX) {
             // a run of small sub-bins: one warp per sub-bin
-            varying_digits_below<THREADS, K>(sm.b, recs, rw, m, p_word, t1 % 8u, key_words);
+            varying_digits_below<THREADS, K>(sm.b, recs, rw, m, p_word, 8u * (t1 % 8u), key_words);
             const u32 nv = sm.b.nv;
             for (u32 ci = d0 + w; ci < d1; ci += NW) {
                 const u32 cb = sm.cbeg[ci] - ga, cc = sm.cbeg[ci + 1] - sm.cbeg[ci];
@@ -608,6 +611,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 bucket_split_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (cta_failed(a.ctrs))
+        return;
     BucketSplitSmem<THREADS, K, KS> &sm = *reinterpret_cast<BucketSplitSmem<THREADS, K, KS> *>(smem_raw);
     const u32 n_items = a.ctrs->bucket_split;
     for (;;) {
@@ -683,6 +688,8 @@ batched_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, PlanArgs a, BatchQue
     __shared__ WorkItem s_item;
     __shared__ int s_kind;  // 0 mid-size, 1 on-chip, -1 none left
     const u32 tid = threadIdx.x;
+    if (cta_failed(a.ctrs))
+        return;
     Counters *const ctrs = a.ctrs;
     const u32 n_mid = ctrs->bmid, n_static = n_mid + (u32)ctrs->block;
     for (;;) {
@@ -832,7 +839,14 @@ u32 bucket_grid()
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (u32)(sms > 0 ? sms : 1);
+    u32 g = (u32)(sms > 0 ? sms : 1);
+    // fewer CTAs keep fewer bins and scratch regions in L2 at once
+    if (const char *v = getenv("RADULS_BUCKET_GRID")) {
+        const u32 want = (u32)strtoul(v, nullptr, 10);
+        if (want >= 1 && want < g)
+            g = want;
+    }
+    return g;
 }
 
 cudaError_t launch_bucket(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, cudaStream_t st)

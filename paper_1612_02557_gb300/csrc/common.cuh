@@ -48,6 +48,93 @@ static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
 // batched sort, arrays [tile_base, tile_base + row) of the offset table.
 enum : u32 { ITEM_IN_TMP = 1u, ITEM_RUN = 2u, ITEM_SEG = 4u };
 
+// Digit windows of the distribution passes.  Key bits are numbered from the
+// least significant bit of the last key word (bit 0) to the most significant
+// bit of word 0 (bit 64W - 1).  A grid item's records agree on every bit at
+// or above `hi`; its pass splits the w bits [hi - w, hi) at once (a digit of
+// 2^w values, w = 1..10).  In the item, `digit` is the byte holding bit
+// hi - 1 (so byte-based consumers see a valid upper bound), flag bits
+// [12, 15) count the top bits of that byte already consumed, and flag bits
+// [8, 12) hold w (0 = 8).  Run items (ITEM_RUN without ITEM_SEG) hold the
+// parent's window instead: `digit` = its lowest bit hi - w, w in bits [8, 12).
+constexpr u32 ITEM_W_SHIFT = 8, ITEM_W_MASK = 15u << 8;
+constexpr u32 ITEM_C_SHIFT = 12, ITEM_C_MASK = 7u << 12;
+constexpr u32 WIDE_MAX = 10;           // widest digit of a distribution pass (1,024 sub-bins)
+constexpr u32 KMAX = 1u << WIDE_MAX;
+
+__host__ __device__ __forceinline__ u32 item_hi(u32 digit, u32 flags)
+{
+    return 8u * digit + 8u - ((flags & ITEM_C_MASK) >> ITEM_C_SHIFT);
+}
+
+__host__ __device__ __forceinline__ u32 item_w(u32 flags)
+{
+    const u32 w = (flags & ITEM_W_MASK) >> ITEM_W_SHIFT;
+    return w ? w : 8u;
+}
+
+// Flags and digit of a grid item whose records agree on the bits >= hi (hi >= 1).
+__host__ __device__ __forceinline__ void grid_pos(u32 hi, u32 w, u32 base_flags, u32 &digit, u32 &flags)
+{
+    digit = (hi - 1u) / 8u;
+    flags = (base_flags & ~(ITEM_W_MASK | ITEM_C_MASK)) | ((8u * digit + 8u - hi) << ITEM_C_SHIFT) |
+            ((w & 15u) << ITEM_W_SHIFT);
+}
+
+// Width of the digit a grid item of `count` records splits next: enough bits
+// that one or two more passes bring its sub-bins down to about `leaf`
+// records, spread evenly over those passes, at least 8 and at most wmax bits,
+// never more than the bits left (hi) or than keep 16 records per sub-bin.
+__host__ __device__ __forceinline__ u32 pick_width(u64 count, u32 hi, u32 leaf, u32 wmax)
+{
+    u32 need = 0;
+    const u64 q = (count + leaf - 1) / (leaf ? leaf : 1u);
+    while (need < 63u && (1ull << need) < q)
+        ++need;
+    u32 w = 8;
+    if (need > 8u) {
+        const u32 levels = (need + wmax - 1u) / wmax;
+        w = (need + levels - 1u) / levels;
+        if (w < 8u)
+            w = 8u;
+    }
+    while (w > 8u && (count >> w) < 16u)
+        --w;
+    if (w > wmax)
+        w = wmax;
+    if (w < 1u)
+        w = 1u;
+    return w < hi ? w : hi;
+}
+
+// Where a window [lo, lo + w) lies in the key words: word wl holds bit lo at
+// shift sl; when the window reaches into the next more significant word wh,
+// that word supplies its low bits above the first (64 - sl) ones.
+struct Window {
+    u32 wl, sl;     // low word and shift
+    u32 wh;         // high word (== wl when the window stays in one word)
+    u32 w;          // width
+};
+
+__host__ __device__ __forceinline__ Window make_window(u32 hi, u32 w, u32 key_words)
+{
+    Window x;
+    const u32 lo = hi - w;
+    x.wl = key_words - 1u - lo / 64u;
+    x.sl = lo % 64u;
+    x.wh = key_words - 1u - (hi - 1u) / 64u;
+    x.w = w;
+    return x;
+}
+
+__device__ __forceinline__ u32 window_of(const Window &x, u64 lowword, u64 highword)
+{
+    u64 v = lowword >> x.sl;
+    if (x.wh != x.wl)
+        v |= highword << (64u - x.sl);
+    return (u32)v & ((1u << x.w) - 1u);
+}
+
 // Device-side counters of one sort.  All list lengths live here so that the
 // pass kernels never need the host to know them.
 struct Counters {
@@ -77,6 +164,8 @@ struct Counters {
     u64 block_bytes;      // bytes read+written by on-chip sorts and copies
     u64 bucket_bytes;     // algorithmic bytes read+written by the mid-size bin kernel
     u64 bucket_items;     // mid-size bins sorted (cumulative)
+    u64 cells_cur;        // look-back status words of the current grid list's chunks
+    u64 cells_next;       // status words claimed by the next grid list
     u32 levels;
     u32 learned_ok;       // 1 while the learned partition passes its balance check
     float learned_ratio;  // max bucket / ideal bucket of the learned partition (0 = not measured)
@@ -95,6 +184,7 @@ struct Caps {
     u32 copy_tiles; // copy tiles
     u32 pad;
     u64 block;      // block items
+    u64 cells;      // look-back status words per level (chunks x digit values of every grid item)
 };
 
 // ---------------------------------------------------------------- learned model
@@ -397,6 +487,18 @@ __device__ __forceinline__ void discard_l2_line(const void *p)
 __device__ __forceinline__ void set_error(Counters *c, u32 code)
 {
     atomicCAS(&c->err, 0u, code);
+}
+
+// True in every thread of the CTA when an earlier step recorded an error (its
+// work lists may then be incomplete, or longer than their storage).  Called
+// once, by the whole CTA, before any other use of the lists.
+__device__ __forceinline__ bool cta_failed(const Counters *c)
+{
+    __shared__ u32 s_failed;
+    if (threadIdx.x == 0)
+        s_failed = ld_relaxed_u32(&c->err);
+    __syncthreads();
+    return s_failed != 0;
 }
 
 __device__ __forceinline__ u32 digit_of_word(u64 w, u32 shift)

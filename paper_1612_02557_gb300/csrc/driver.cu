@@ -18,10 +18,9 @@
 
 namespace raduls {
 
-u32 scatter_tile_of(int var);
 u32 block_cap_of(int var);
 
-// Distribution variants that fit a record width (see SCATTER_VARIANTS).
+// Distribution variants that fit a record width (see WSCATTER_VARIANTS).
 bool scatter_variant_fits(int v, u32 rw)
 {
     switch (v) {
@@ -29,10 +28,12 @@ bool scatter_variant_fits(int v, u32 rw)
         return rw == 1;
     case 1:
     case 5:
-    case 6:
-    case 7:
+    case 8:
         return rw == 2;
+    case 6:
+        return rw == 1;
     case 2:
+    case 7:
         return rw == 4;
     case 3:
         return rw <= 8;
@@ -52,6 +53,8 @@ struct Tuned {
     int scat_var = 0;
     u32 cap_b = 0;
     u32 bucket_max = 0;
+    u32 wmax = 0;   // widest digit of a distribution pass (0: default)
+    u32 leaf = 0;   // sub-bin size the digit widths aim at (0: default)
 };
 constexpr int TUNE_DEVICES = 64;
 Tuned g_tuned[TUNE_DEVICES][2][33];
@@ -65,16 +68,18 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     Shape s{};
     s.rw = rw;
     s.key_words = key_words;
-    s.tile_h = 16384;
+    s.tile_h = 65536;   // records per chunk of a distribution pass
     s.tile_c = 65536;
+    // default distribution shapes: two CTAs per SM with 8-bit digits (the
+    // autotuner also times the one-CTA shapes that take digits of up to 10 bits)
     if (rw == 1) {
-        s.scat_var = 0;
+        s.scat_var = 6;
         s.block_var = 0;
     } else if (rw == 2) {
-        s.scat_var = 1;
+        s.scat_var = 5;
         s.block_var = 1;
     } else if (rw == 4) {
-        s.scat_var = 2;
+        s.scat_var = 7;
         s.block_var = 2;
     } else if (rw <= 8) {
         s.scat_var = 3;
@@ -101,6 +106,8 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
             cudaGetLastError();
         }
     }
+    s.wmax = WIDE_MAX;
+    s.leaf = 0;
     if (t.valid) {
         if (scatter_variant_fits(t.scat_var, rw))
             s.scat_var = t.scat_var;
@@ -108,7 +115,17 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
             s.cap_b = t.cap_b;
         if (s.bucket_var >= 0)
             s.bucket_max = t.bucket_max;
+        if (t.wmax >= 8 && t.wmax <= WIDE_MAX)
+            s.wmax = t.wmax;
+        s.leaf = t.leaf;
     }
+    if (const char *v = getenv("RADULS_WMAX")) {
+        const u32 want = (u32)strtoul(v, nullptr, 10);
+        if (want >= 8 && want <= WIDE_MAX)
+            s.wmax = want;
+    }
+    if (const char *v = getenv("RADULS_LEAF"))
+        s.leaf = (u32)strtoul(v, nullptr, 10);
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
         if (scatter_variant_fits(want, rw))
@@ -116,7 +133,11 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     }
     if (const char *v = getenv("RADULS_BUCKET_MAX"))
         s.bucket_max = s.bucket_var < 0 ? 0u : (u32)strtoul(v, nullptr, 10);
-    s.tile_s = scatter_tile_of(s.scat_var);
+    s.tile_s = wscatter_tile_of(s.scat_var);
+    while (s.wmax > 8u && (1u << s.wmax) > wscatter_kmax_of(s.scat_var))
+        --s.wmax;  // the variant handles no wider digit
+    if (s.leaf == 0 || s.leaf > s.cap_b)
+        s.leaf = s.cap_b / 4u * 3u;  // sub-bins of about 3/4 of the on-chip class: the largest still fit
     if (s.bucket_max > BUCKET_IDX_MAX)  // positions inside a mid-size bin are 16-bit
         s.bucket_max = BUCKET_IDX_MAX;
     if (s.bucket_max <= s.cap_b)
@@ -222,6 +243,7 @@ struct Lists {
     WorkItem *copies;
     u32 *tile_hist;
     u32 *tile_copy;
+    u64 *cell[2];  // first look-back status word of every grid item (current / next list)
     Caps caps;
 };
 
@@ -313,7 +335,7 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
         block_cap = n + 4;
     if (grid_cap > 0xffffffffull || hist_tiles > 0xffffffffull || copy_tiles > 0xffffffffull)
         return cudaErrorInvalidValue;
-    size_t off = 0, o_grid0, o_grid1, o_scat, o_bkt0, o_bkt1, o_bkts, o_blocks, o_copies, o_th, o_tc;
+    size_t off = 0, o_grid0, o_grid1, o_scat, o_bkt0, o_bkt1, o_bkts, o_blocks, o_copies, o_th, o_tc, o_c0, o_c1;
     o_grid0 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_grid1 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_scat = off; off = align256(off + grid_cap * sizeof(WorkItem));
@@ -324,6 +346,8 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
     o_copies = off; off = align256(off + copy_cap * sizeof(WorkItem));
     o_th = off; off = align256(off + hist_tiles * 4);
     o_tc = off; off = align256(off + copy_tiles * 4);
+    o_c0 = off; off = align256(off + grid_cap * 8);
+    o_c1 = off; off = align256(off + grid_cap * 8);
     cudaError_t e = ensure(wk.lists, off, false);
     if (e != cudaSuccess)
         return e;
@@ -338,12 +362,18 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
     L.copies = (WorkItem *)(b + o_copies);
     L.tile_hist = (u32 *)(b + o_th);
     L.tile_copy = (u32 *)(b + o_tc);
+    L.cell[0] = (u64 *)(b + o_c0);
+    L.cell[1] = (u64 *)(b + o_c1);
     L.caps.grid = (u32)grid_cap;
     L.caps.hist_tiles = (u32)hist_tiles;
     L.caps.copy = (u32)copy_cap;
     L.caps.copy_tiles = (u32)copy_tiles;
     L.caps.block = block_cap;
     L.caps.scat_tiles = 0;
+    // look-back status words of one level: a grid item of c records has
+    // ceil(c / tile_h) chunks of 2^w words, 2^w <= max(256, c / 16)
+    const double per_rec = 256.0 / (double)(s.cap_b + 1u) > 1.0 / 16.0 ? 256.0 / (double)(s.cap_b + 1u) : 1.0 / 16.0;
+    L.caps.cells = (u64)(2.0 * per_rec * (double)n) + 16ull * KMAX;
     return cudaSuccess;
 }
 
@@ -364,11 +394,8 @@ cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B
     B.hist = (u64 *)wk.hist.p;
     B.orand = (u64 *)((char *)wk.hist.p + hb);
     B.dlight = (u64 *)((char *)wk.hist.p + hb + ob);
-    const u64 st_tiles = n / s.tile_s + n_grid + 2;
-    if (st_tiles > 0xffffffffull)
-        return cudaErrorInvalidValue;
     bool grew = false;
-    e = ensure(wk.status, st_tiles * RADIX * 8, true, &grew, st);
+    e = ensure(wk.status, caps.cells * 8, true, &grew, st);
     if (e != cudaSuccess)
         return e;
     if (grew) {  // fresh zeroed words: restart the epochs
@@ -376,14 +403,12 @@ cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B
         if (e != cudaSuccess)
             return e;
     }
-    e = ensure(wk.tiles, st_tiles * 4, false);
+    e = ensure(wk.tiles, (size_t)caps.hist_tiles * 4, false);
     if (e != cudaSuccess)
         return e;
     B.status = (u64 *)wk.status.p;
     B.tile_scat = (u32 *)wk.tiles.p;
-    caps.scat_tiles = (u32)(wk.status.bytes / (RADIX * 8));
-    if ((u64)caps.scat_tiles * 4 > wk.tiles.bytes)
-        caps.scat_tiles = (u32)(wk.tiles.bytes / 4);
+    caps.scat_tiles = caps.hist_tiles;
     return cudaSuccess;
 }
 
@@ -624,8 +649,12 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
     const u32 bmax = step_api ? 0u : s.bucket_max;
     if (bmax)
         CK(ensure(wk.bscratch, (size_t)bucket_grid() * bmax * bucket_slot_bytes(j.rw), false));
+    // the learned first partition's root is the top byte's histogram: its first
+    // pass splits exactly that byte
+    const u32 init_wmax = (step_api || (may_learn && j.mode == 2)) ? 0u : s.wmax;
     TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n, step_api ? j.digit : top,
-                                      s.cap_b, s.tile_h, step_api ? 1u : 0u, L.bkt[0], bmax, st));
+                                      s.cap_b, s.tile_h, step_api ? 1u : 0u, L.bkt[0], bmax, L.cell[0], s.leaf,
+                                      init_wmax, st));
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
         c.wait_ns = g_wait_ns;
@@ -663,24 +692,39 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         a.buckets_split = L.bkt_split;
         a.bucket_max = bmax;
         a.bucket_scratch = (u64 *)wk.bscratch.p;
+        a.cell_cur = L.cell[cur];
+        a.cell_next = L.cell[cur ^ 1];
+        a.leaf = s.leaf;
+        a.wmax = s.wmax;
+        a.status = (u64 *)wk.status.p;
         if (n_grid > 0) {
             LevelBufs B{};
             CK(work_level(wk, s, j.n, n_grid, B, L.caps, st));
             a.caps = L.caps;  // the level's buffers fix the distribution tile capacity
+            a.status = B.status;
             const Model *model = learned ? c.mdl.model : nullptr;
-            TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
-            TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
-                                             wk.ctrs, model, st));
+            TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, (j.hist_out || learned) ? 1u : 0u, st));
             if (j.hist_out) {
+                // histogram only (raduls_histogram): one traversal, counts per value
+                TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
+                                                 wk.ctrs, model, st));
                 CK(cudaMemcpyAsync(j.hist_out, B.hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
                 break;
             }
+            TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+            TIMED(RADULS_K_HIST, launch_whist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status,
+                                              B.orand, B.dlight, wk.ctrs, model, wk.epoch, c.wait_ns, c.inject_tile,
+                                              st));
+            c.inject_tile = ~0u;
             if (level == 0 && may_learn) {
                 // the first pass's digit histogram is the model's root; AUTO
                 // keeps the plain passes (the learned first partition is taken
                 // only when asked for)
                 const bool use = (j.mode == 2);
                 if (use) {
+                    // the root bin's histogram of its top byte: its last chunk's counts
+                    const u64 nch = (j.n + s.tile_h - 1) / s.tile_h;
+                    TIMED(RADULS_K_SETUP, launch_status_counts(B.status + (nch - 1) * RADIX, B.hist, RADIX, st));
                     const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
                     int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);
                     if (rc)
@@ -688,10 +732,13 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
                     learned = true;
                     // restart the level on the model's top digit
                     TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n,
-                                                      DIGIT_LEARNED_HI, s.cap_b, s.tile_h, 1u, nullptr, 0u, st));
-                    TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, st));
-                    TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand,
-                                                     B.dlight, wk.ctrs, c.mdl.model, st));
+                                                      DIGIT_LEARNED_HI, s.cap_b, s.tile_h, 1u, nullptr, 0u, L.cell[0],
+                                                      s.leaf, 0u, st));
+                    TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, 1u, st));
+                    TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+                    TIMED(RADULS_K_HIST, launch_whist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status,
+                                                      B.orand, B.dlight, wk.ctrs, c.mdl.model, wk.epoch, c.wait_ns,
+                                                      ~0u, st));
                     model = c.mdl.model;
                 }
             }
@@ -701,10 +748,8 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             a.orand = B.orand;
             a.tile_scat = B.tile_scat;
             TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-            TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
-            TIMED(RADULS_K_SCATTER, launch_scatter(s, j.in, j.tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs,
-                                                   wk.epoch, c.wait_ns, c.inject_tile, model, st));
-            c.inject_tile = ~0u;
+            TIMED(RADULS_K_SCATTER, launch_wscatter(s, j.in, j.tmp, L.scat, B.tile_scat, L.cell[cur], B.status,
+                                                    wk.ctrs, model, c.wait_ns, st));
         }
         if (n_bkt > 0 && n_grid == 0 && j.hout && !wk.h_ctrs->block && !wk.h_ctrs->copy) {
             // the last mid-size level of an end-to-end sort: position windows,
@@ -802,7 +847,7 @@ struct BatchGraph {
     u64 n = 0;
     u32 n_segs = 0, rw = 0, kw = 0;
     int scat_var = -1;
-    u32 cap_b = 0, bucket_max = 0;  // the shape the graph was captured with
+    u32 cap_b = 0, bucket_max = 0, wmax = 0, leaf = 0;  // the shape the graph was captured with
     void *ws[6] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
 };
 
@@ -813,12 +858,14 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
 {
     const u32 top = 8u * kw - 1u;
     CK(launch_batched_init(off, n_segs, L.grid[0], L.blocks, L.tile_hist, wk.ctrs, L.caps, top, s.cap_b, s.tile_h,
-                           const_cast<WorkItem *>(q.mid), s.bucket_max, st));
+                           const_cast<WorkItem *>(q.mid), s.bucket_max, L.cell[0], s.leaf, s.wmax, st));
     int cur = 0;
     const u32 levels = 8u * kw;
     for (u32 level = 0; level < levels; ++level) {
-        CK(launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, L.caps.grid, st));
-        CK(launch_hist(s, in, tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight, wk.ctrs, nullptr, st));
+        CK(launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, L.caps.grid, 0u, st));
+        CK(launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+        CK(launch_whist(s, in, tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status, B.orand, B.dlight, wk.ctrs,
+                        nullptr, wk.epoch, c.wait_ns, ~0u, st));
         PlanArgs a{};
         a.grid_cur = L.grid[cur];
         a.grid_next = L.grid[cur ^ 1];
@@ -846,10 +893,13 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
         a.buckets_split = L.bkt_split;
         a.bucket_max = s.bucket_max;
         a.bucket_scratch = (u64 *)wk.bscratch.p;
+        a.status = B.status;
+        a.cell_cur = L.cell[cur];
+        a.cell_next = L.cell[cur ^ 1];
+        a.leaf = s.leaf;
+        a.wmax = s.wmax;
         CK(launch_plan(a, 0, st));
-        CK(launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
-        CK(launch_scatter(s, in, tmp, L.scat, B.tile_scat, B.hist, B.status, wk.ctrs, wk.epoch, c.wait_ns, ~0u,
-                          nullptr, st));
+        CK(launch_wscatter(s, in, tmp, L.scat, B.tile_scat, L.cell[cur], B.status, wk.ctrs, nullptr, c.wait_ns, st));
         if (a.bucket_max)
             CK(launch_bucket(s, in, tmp, a, st));
         CK(launch_advance(wk.ctrs, st));
@@ -919,7 +969,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         same_ws = same_ws && bg.ws[i] == ws[i];
     const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
                      bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws && bg.scat_var == s.scat_var &&
-                     bg.cap_b == s.cap_b && bg.bucket_max == s.bucket_max;
+                     bg.cap_b == s.cap_b && bg.bucket_max == s.bucket_max && bg.wmax == s.wmax && bg.leaf == s.leaf;
     if (!hit) {
         if (bg.exec) {
             cudaGraphExecDestroy(bg.exec);
@@ -953,6 +1003,8 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         bg.scat_var = s.scat_var;
         bg.cap_b = s.cap_b;
         bg.bucket_max = s.bucket_max;
+        bg.wmax = s.wmax;
+        bg.leaf = s.leaf;
     }
     CK(cudaGraphLaunch(bg.exec, st));
     return RADULS_OK;
@@ -1360,99 +1412,131 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     const bool batched = d_seg_offsets != nullptr;
     const u32 rw = rec_bytes / 8u, kw = key_bytes / 8u;
     cudaStream_t st = (cudaStream_t)stream;
-    // candidates: every distribution variant of this record width, the on-chip
-    // class at its full and half size, the mid-size class off / half / full
+    // Candidates, one setting at a time from the defaults (coordinate descent):
+    // every distribution variant of this record width, the widest digit of a
+    // distribution pass (12 down to 8 bits), the sub-bin size the digit widths
+    // aim at, the on-chip class at its full and half size, the mid-size class
+    // full / half / off.  A later candidate must beat the current choice by
+    // more than TIE_FRAC: within timing noise the default, larger size classes
+    // stay, which suits inputs less regular than the tuner's seeded records.
     Tuned none{};
     g_force = &none;
     const Shape base = choose_shape(rw, kw, batched);
     g_force = nullptr;
-    // Candidates go from the default shape outward (its distribution variant
-    // first, the full size classes first), and a later one must beat the
-    // current choice by more than TIE_FRAC: within timing noise the default,
-    // larger size classes stay, which suits inputs less regular than the
-    // tuner's seeded records.
     constexpr float TIE_FRAC = 0.01f;
-    int vars[8];
-    int nv = 0;
-    vars[nv++] = base.scat_var;
-    for (int v = 0; v < 8; ++v)
-        if (v != base.scat_var && scatter_variant_fits(v, rw) && !((v == 3 || v == 4) && rw <= 4))
-            vars[nv++] = v;
-    const u32 caps[2] = {base.cap_b, base.cap_b / 2};
-    const u32 bmaxes[3] = {base.bucket_max, base.bucket_max / 2, 0u};
-    const int nb = base.bucket_max ? 3 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         return RADULS_ERR_CUDA;
     }
     Tuned best{};
+    best.valid = true;
+    best.scat_var = base.scat_var;
+    best.cap_b = base.cap_b;
+    best.bucket_max = base.bucket_max;
+    best.wmax = base.wmax;
+    best.leaf = base.leaf;
     float best_ms = 0.f;
+    bool have_best = false;
     u32 timed = 0;
     rc = RADULS_OK;
-    for (int vi = 0; vi < nv && rc == RADULS_OK; ++vi)
-        for (int ci = 0; ci < 2 && rc == RADULS_OK; ++ci)
-            for (int bi = 0; bi < nb && rc == RADULS_OK; ++bi) {
-                Tuned t{};
-                t.valid = true;
-                t.scat_var = vars[vi];
-                t.cap_b = caps[ci];
-                t.bucket_max = bmaxes[bi] > caps[ci] ? bmaxes[bi] : 0u;
-                if (bmaxes[bi] != 0u && t.bucket_max == 0)
-                    continue;  // collapses to "off", which is a candidate of its own
-                float ms_min = 0.f;
-                for (int rep = 0; rep < 2 && rc == RADULS_OK; ++rep) {
-                    tune_fill_kernel<<<1024, 256, 0, st>>>((u64 *)in, n_recs * rw, 0x5241445553ull + rep);
-                    if (cudaGetLastError() != cudaSuccess) {
-                        rc = RADULS_ERR_CUDA;
-                        break;
-                    }
-                    g_force = &t;
-                    cudaEventRecord(e0, st);
-                    {
-                        std::lock_guard<std::mutex> g(c->mu);
-                        cudaError_t e = ctx_init(*c);
-                        if (e != cudaSuccess) {
-                            rc = to_status(e);
-                        } else if (batched) {
-                            rc = run_batched(*c, dev, (u64 *)in, (u64 *)tmp, (const u64 *)d_seg_offsets, n_segs,
-                                             n_recs, rw, kw, st);
-                        } else {
-                            SortJob j{};
-                            j.in = (u64 *)in;
-                            j.tmp = (u64 *)tmp;
-                            j.n = n_recs;
-                            j.rw = rw;
-                            j.kw = kw;
-                            j.mode = 1;
-                            j.train_steps = 16u;
-                            rc = run_sort(*c, c->main, j, st);
-                        }
-                    }
-                    g_force = nullptr;
-                    cudaEventRecord(e1, st);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        cudaGetLastError();
-                        rc = RADULS_ERR_CUDA;
-                        break;
-                    }
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    ms_min = (rep == 0 || ms < ms_min) ? ms : ms_min;
-                }
-                if (rc == RADULS_OK) {
-                    const int srt = raduls_stream_status(stream);
-                    if (srt != RADULS_OK)
-                        rc = srt;
-                }
-                if (rc != RADULS_OK)
-                    break;
-                ++timed;
-                if (!best.valid || ms_min < best_ms * (1.f - TIE_FRAC)) {
-                    best = t;
-                    best_ms = ms_min;
+    auto time_one = [&](const Tuned &t, float &ms_min) {
+        for (int rep = 0; rep < 2 && rc == RADULS_OK; ++rep) {
+            tune_fill_kernel<<<1024, 256, 0, st>>>((u64 *)in, n_recs * rw, 0x5241445553ull + rep);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = RADULS_ERR_CUDA;
+                break;
+            }
+            g_force = &t;
+            cudaEventRecord(e0, st);
+            {
+                std::lock_guard<std::mutex> g(c->mu);
+                cudaError_t e = ctx_init(*c);
+                if (e != cudaSuccess) {
+                    rc = to_status(e);
+                } else if (batched) {
+                    rc = run_batched(*c, dev, (u64 *)in, (u64 *)tmp, (const u64 *)d_seg_offsets, n_segs, n_recs, rw,
+                                     kw, st);
+                } else {
+                    SortJob j{};
+                    j.in = (u64 *)in;
+                    j.tmp = (u64 *)tmp;
+                    j.n = n_recs;
+                    j.rw = rw;
+                    j.kw = kw;
+                    j.mode = 1;
+                    j.train_steps = 16u;
+                    rc = run_sort(*c, c->main, j, st);
                 }
             }
+            g_force = nullptr;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                rc = RADULS_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_min = (rep == 0 || ms < ms_min) ? ms : ms_min;
+        }
+        if (rc == RADULS_OK) {
+            const int srt = raduls_stream_status(stream);
+            if (srt != RADULS_OK)
+                rc = srt;
+        }
+        if (rc != RADULS_OK)
+            return;
+        ++timed;
+        if (!have_best || ms_min < best_ms * (1.f - TIE_FRAC)) {
+            best = t;
+            best_ms = ms_min;
+            have_best = true;
+        }
+    };
+    float ms = 0.f;
+    time_one(best, ms);
+    for (int v = 0; v < 9 && rc == RADULS_OK; ++v) {
+        if (v == base.scat_var || !scatter_variant_fits(v, rw) || ((v == 3 || v == 4) && rw <= 4))
+            continue;
+        Tuned t = best;
+        t.scat_var = v;
+        if ((1u << t.wmax) > wscatter_kmax_of(v))
+            t.wmax = 8;
+        time_one(t, ms);
+    }
+    for (u32 wm = WIDE_MAX; wm >= 8u && rc == RADULS_OK; --wm) {
+        if (wm == best.wmax || (1u << wm) > wscatter_kmax_of(best.scat_var))
+            continue;
+        Tuned t = best;
+        t.wmax = wm;
+        time_one(t, ms);
+    }
+    const u32 leaves[2] = {base.cap_b / 2u, WARP_BIN / 2u};
+    for (int li = 0; li < 2 && rc == RADULS_OK; ++li) {
+        if (leaves[li] == best.leaf || leaves[li] < 16u)
+            continue;
+        Tuned t = best;
+        t.leaf = leaves[li];
+        time_one(t, ms);
+    }
+    if (rc == RADULS_OK && base.cap_b / 2u > WARP_BIN) {
+        Tuned t = best;
+        t.cap_b = base.cap_b / 2u;
+        if (t.leaf > t.cap_b)
+            t.leaf = t.cap_b / 2u;
+        if (t.bucket_max && t.bucket_max <= t.cap_b)
+            t.bucket_max = 0;
+        time_one(t, ms);
+    }
+    const u32 bmaxes[2] = {base.bucket_max / 2u, 0u};
+    for (int bi = 0; bi < 2 && base.bucket_max && rc == RADULS_OK; ++bi) {
+        Tuned t = best;
+        t.bucket_max = bmaxes[bi] > t.cap_b ? bmaxes[bi] : 0u;
+        if (t.bucket_max == best.bucket_max)
+            continue;
+        time_one(t, ms);
+    }
     g_force = nullptr;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1464,11 +1548,13 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     }
     if (out) {
         out->scatter_variant = best.scat_var;
-        out->scatter_tile = scatter_tile_of(best.scat_var);
+        out->scatter_tile = wscatter_tile_of(best.scat_var);
         out->block_cap = best.cap_b;
         out->bucket_max = best.bucket_max;
         out->best_ms = best_ms;
         out->candidates = timed;
+        out->digit_bits = best.wmax;
+        out->leaf = best.leaf;
     }
     return RADULS_OK;
 }

@@ -17,24 +17,39 @@ struct Shape {
     int scat_var;    // distribution kernel variant
     int block_var;   // on-chip sort kernel variant
     int bucket_var;  // mid-size bin kernel variant (-1: none for this record width)
+    u32 leaf;        // sub-bin size the distribution passes' digit widths aim at
+    u32 wmax;        // widest digit of a distribution pass (bits, 8..WIDE_MAX)
 };
 
 Shape choose_shape(u32 rw, u32 key_words, bool batched = false);
 
 // Persistent-grid sizes (CTAs) of each kernel for a shape on the current device.
 u32 hist_grid(const Shape &s);
-u32 scatter_grid(const Shape &s);
 u32 block_grid(const Shape &s);
 u32 copy_grid();
 
 cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items,
                         const u32 *tile_item, u64 *hist, u64 *orand, u64 *dlight, Counters *ctrs,
                         const Model *model, cudaStream_t st);
-cudaError_t launch_scatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                           const u64 *bases, u64 *status, Counters *ctrs, const u32 *epoch, u64 wait_ns,
-                           u32 inject_tile, const Model *model, cudaStream_t st);
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks,
                               Counters *ctrs, const u64 *seg_off, cudaStream_t st);
+
+// The distribution pass over chunks (wide.cu): a histogram of every chunk's
+// digit window whose counts are chained along each bin's chunks by a
+// decoupled look-back (status words: per chunk and digit value, the records
+// of that value in the bin's chunks up to and including it), then a scatter in
+// which every CTA distributes whole chunks on its own.
+cudaError_t launch_whist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items, const u32 *tile_item,
+                         const u64 *cell_off, u64 *status, u64 *orand, u64 *dlight, Counters *ctrs, const Model *model,
+                         const u32 *epoch, u64 wait_ns, u32 inject_chunk, cudaStream_t st);
+cudaError_t launch_wscatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
+                            const u64 *cell_off, const u64 *status, Counters *ctrs, const Model *model, u64 wait_ns,
+                            cudaStream_t st);
+u32 wscatter_tile_of(int var);
+u32 wscatter_kmax_of(int var);  // most digit values a variant handles
+// out[i] = the count held by status word row[i] (i < k).
+cudaError_t launch_status_counts(const u64 *row, u64 *out, u32 k, cudaStream_t st);
+u32 wscatter_grid(const Shape &s);
 
 // Planning kernels (plan.cu).
 struct PlanArgs {
@@ -65,6 +80,11 @@ struct PlanArgs {
     const u32 *bucket_order;  // non-null: the mid-size kernel takes only window bucket_window of this list
     const u32 *bucket_wstart; // (bin indices grouped by position window; see launch_bucket_windows)
     u32 bucket_window;
+    u64 *status;              // look-back status words of this level's chunks (then the digit starts)
+    const u64 *cell_cur;      // first status word of every current grid item (by slot)
+    u64 *cell_next;           // same for the next grid list
+    u32 leaf;                 // sub-bin size the digit widths aim at
+    u32 wmax;                 // widest digit of a pass (bits)
 };
 
 // Position windows of the last mid-size level (an end-to-end sort copies each
@@ -79,13 +99,17 @@ inline size_t bucket_slot_bytes(u32 rw) { return rw == 2 ? 32u : (size_t)rw * 8u
 
 __device__ __forceinline__ u32 ceil_div_u64(u64 a, u32 b) { return (u32)((a + b - 1) / b); }
 
-// Append a bin to the next grid list and map its histogram tiles.
-__device__ __forceinline__ void append_grid(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+// Append a learned-digit or key-window bin to the next grid list, claim its
+// look-back status words (chunks x 2^w) and map its histogram chunks.
+__device__ __forceinline__ void append_grid_item(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags,
+                                                 u32 w)
 {
     const u32 slot = atomicAdd(&a.ctrs->grid_next, 1u);
     const u32 nt = ceil_div_u64(count, a.tile_h);
     const u32 tb = atomicAdd(&a.ctrs->grid_next_tiles, nt);
-    if (slot >= a.caps.grid || (u64)tb + nt > a.caps.hist_tiles) {
+    const u64 cells = (u64)nt << w;
+    const u64 co = atomicAdd(&a.ctrs->cells_next, cells);
+    if (slot >= a.caps.grid || (u64)tb + nt > a.caps.hist_tiles || co + cells > a.caps.cells) {
         set_error(a.ctrs, ST_INTERNAL);
         return;
     }
@@ -97,16 +121,19 @@ __device__ __forceinline__ void append_grid(const PlanArgs &a, u64 begin, u64 co
     it.tile_base = tb;
     it.row = slot;
     a.grid_next[slot] = it;
+    a.cell_next[slot] = co;
     for (u32 j = 0; j < nt; ++j)
         a.tile_hist[tb + j] = slot;
 }
 
-// Append a bin that still needs sorting from digit `digit` down: a mid-size
-// bin of a plain digit goes to the next level's mid-size list (no histogram
-// pass: its kernel counts for itself), any other to the next grid list.
-__device__ __forceinline__ void append_bin(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+// Append a bin whose records agree on every key bit at or above `hi`: a
+// mid-size bin goes to the next level's mid-size list (no histogram pass: its
+// kernel counts for itself, from the byte holding bit hi - 1 down), any other
+// to the next grid list with a digit width picked for its size.
+__device__ __forceinline__ void append_bin_hi(const PlanArgs &a, u64 begin, u64 count, u32 hi, u32 flags)
 {
-    if (a.bucket_max && digit < DIGIT_LEARNED_HI && count <= a.bucket_max) {
+    flags &= ~(ITEM_W_MASK | ITEM_C_MASK);
+    if (a.bucket_max && count <= a.bucket_max) {
         const u32 slot = atomicAdd(&a.ctrs->bucket_next, 1u);
         if (slot >= a.caps.grid) {
             set_error(a.ctrs, ST_INTERNAL);
@@ -115,14 +142,23 @@ __device__ __forceinline__ void append_bin(const PlanArgs &a, u64 begin, u64 cou
         WorkItem it;
         it.begin = begin;
         it.count = count;
-        it.digit = digit;
+        it.digit = (hi - 1u) / 8u;
         it.flags = flags;
         it.tile_base = 0;
         it.row = 0;
         a.buckets_next[slot] = it;
         return;
     }
-    append_grid(a, begin, count, digit, flags);
+    const u32 w = pick_width(count, hi, a.leaf, a.wmax);
+    u32 digit, fl;
+    grid_pos(hi, w, flags, digit, fl);
+    append_grid_item(a, begin, count, digit, fl, w);
+}
+
+// Same, for a bin whose key bytes above `digit` agree (byte-based callers).
+__device__ __forceinline__ void append_bin(const PlanArgs &a, u64 begin, u64 count, u32 digit, u32 flags)
+{
+    append_bin_hi(a, begin, count, 8u * digit + 8u, flags);
 }
 
 // Mid-size bins (bucketsort.cu): every bin of a.buckets_cur is sorted by one
@@ -144,8 +180,11 @@ cudaError_t launch_batched_persistent(const Shape &s, u64 *in, u64 *tmp, const P
                                       const u64 *seg_off, u64 wait_ns, cudaStream_t st);
 
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
-                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, cudaStream_t st);
-cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint,
+                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, u64 *cell0,
+                        u32 leaf, u32 wmax, cudaStream_t st);
+// Clear the level's OR / AND words (and, zero_rows, its per-bin histogram rows
+// for the histogram-only traversal and the learned balance counts).
+cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows,
                         cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
@@ -154,7 +193,7 @@ cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u
 cudaError_t launch_bucket_window_reset(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
                                 Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
-                                u32 bucket_max, cudaStream_t st);
+                                u32 bucket_max, u64 *cell0, u32 leaf, u32 wmax, cudaStream_t st);
 cudaError_t launch_check_drained(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st);
 cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,

@@ -71,14 +71,14 @@ __device__ __forceinline__ int key_cmp(const u64 *recs, u32 rw, u32 a, u32 b, u3
     return 0;
 }
 
-// Key digits below digit (p_word, p_byte) that vary anywhere in the m records
-// of `recs` (OR / AND of each key word over the records): the list
-// sm.vword/vshift (most significant first) and its length sm.nv.  p_byte is
-// the number of bytes of p_word below the split digit that may vary (8 = all).
+// Key digits below a split that vary anywhere in the m records of `recs` (OR
+// / AND of each key word over the records): the list sm.vword/vshift (most
+// significant first) and its length sm.nv.  p_bits is the number of low bits
+// of key word p_word below the split that may vary (64 = all of them).
 // Must be called by the whole CTA.
 template <int THREADS, int K>
 __device__ __forceinline__ void varying_digits_below(BlockSmem<THREADS, K> &sm, const u64 *recs, u32 rw, u32 m,
-                                                     u32 p_word, u32 p_byte, u32 key_words)
+                                                     u32 p_word, u32 p_bits, u32 key_words)
 {
     constexpr int NW = THREADS / 32;
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
@@ -107,8 +107,8 @@ __device__ __forceinline__ void varying_digits_below(BlockSmem<THREADS, K> &sm, 
                 a2 &= sm.red_and[i];
             }
             u64 diff = o2 ^ a2;
-            if (wi == p_word && p_byte < 8u)
-                diff &= (p_byte == 0) ? 0ull : ((1ull << (8u * p_byte)) - 1ull);
+            if (wi == p_word && p_bits < 64u)
+                diff &= (p_bits == 0) ? 0ull : ((1ull << p_bits) - 1ull);
             sm.diff[wi] = diff;
         }
         __syncthreads();
@@ -306,6 +306,167 @@ __device__ __forceinline__ void block_path(BlockSmem<THREADS, K> &sm, const u64 
         for (int v = (int)nv - 1; v >= 0; --v)
             lsd_pass<THREADS, K>(sm, recs, rw, m, kv, sm.vword[v], sm.vshift[v], id);
     }
+}
+
+// ------------------------------------------------------- code-group path
+
+constexpr u32 CODE_BITS = 12;                // the code: up to the bin's 12 highest varying key bits
+constexpr u32 CODE_N = 1u << CODE_BITS;
+constexpr u32 CODE_GMAX = 64;                // largest code group settled by comparison ranks
+
+// Whole-CTA stable sort of one bin of m records held in shared memory, for
+// uniform-like keys.  The key bits below the bin's known common prefix (its
+// records agree on every bit at or above `hi`) form a code: one more bit than
+// m needs, at most 12, at least 8.  The codes are counted and turned into
+// group starts (an exclusive prefix, Sec. 1); every record takes the next
+// slot of its code's group (an atomic, so the slots inside a group are in no
+// particular order); then each record's final place inside its group is the
+// number of members with a smaller key, or an equal key and a smaller
+// position in the bin -- exactly the stable order, since the bin's records are
+// in input order.  The records are written to `out` once, in their final
+// order.  When a code group holds more than CODE_GMAX records, the OR / AND
+// of the key word below `hi` moves the code down past bits the whole bin
+// shares and the count is taken again; if groups are still too big (heavy
+// duplicates) nothing is written and false is returned: the caller then sorts
+// the bin another way.  Needs THREADS * K >= CODE_N (its code counters live in
+// the ranking scratch).
+template <int THREADS, int K, int RW>
+__device__ __forceinline__ bool block_code_sort(BlockSmem<THREADS, K> &sm, const u64 *recs, u32 rw, u32 m, u32 hi,
+                                                u32 key_words, u64 *out)
+{
+    constexpr int NW = THREADS / 32;
+    static_assert(sizeof(RankSmem<THREADS>::cnt) >= CODE_N * 4, "code counters fit the ranking scratch");
+    static_assert(THREADS * K >= (int)CODE_N, "code cursors fit the exchange buffer");
+    const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
+    u32 *cnt = &sm.rank.cnt[0][0];
+    u32 hv = hi;
+    if (hv == 0) {
+        // every key bit is shared: the input order is the stable order
+        for (u32 e = tid; e < m; e += THREADS)
+            copy_record<RW>(out + (u64)e * rw, recs + (u64)e * rw, rw);
+        return true;
+    }
+    const u32 wt = key_words - 1u - (hv - 1u) / 64u;  // the key word holding bit hv - 1
+    u32 cb = 8, NC = 256;
+    Window cw;
+    for (int attempt = 0;; ++attempt) {
+        cb = 8;
+        while (cb < CODE_BITS && (1u << cb) < 2u * m)
+            ++cb;
+        if (cb > hv)
+            cb = hv;
+        NC = 1u << cb;
+        cw = make_window(hv, cb, key_words);
+        for (u32 i = tid; i < NC; i += THREADS)
+            cnt[i] = 0;
+        __syncthreads();
+        u64 vor = 0, vand = ~0ull;
+        for (u32 e = tid; e < m; e += THREADS) {
+            const u64 lw = recs[(u64)e * rw + cw.wl];
+            const u64 hw = cw.wh != cw.wl ? recs[(u64)e * rw + cw.wh] : lw;
+            atomicAdd(&cnt[window_of(cw, lw, hw)], 1u);
+            if (attempt == 0) {
+                const u64 x = recs[(u64)e * rw + wt];
+                vor |= x;
+                vand &= x;
+            }
+        }
+        if (attempt == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vor |= __shfl_xor_sync(FULL_MASK, vor, o);
+                vand &= __shfl_xor_sync(FULL_MASK, vand, o);
+            }
+            if (lane == 0) {
+                sm.red_or[w] = vor;
+                sm.red_and[w] = vand;
+            }
+        }
+        __syncthreads();
+        const u32 per = NC > THREADS ? NC / THREADS : 1u;
+        u32 big = 0;
+        if (tid * per < NC)
+            for (u32 i = 0; i < per; ++i)
+                big |= cnt[tid * per + i] > CODE_GMAX ? 1u : 0u;
+        if (attempt == 0 && tid == 0) {
+            u64 o2 = 0, a2 = ~0ull;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                o2 |= sm.red_or[i];
+                a2 &= sm.red_and[i];
+            }
+            sm.diff[0] = o2 ^ a2;
+        }
+        if (!__syncthreads_or(big))
+            break;
+        if (attempt > 0)
+            return false;
+        // skip the top bits every record shares, within the word below hi
+        const u32 bits = (hv - 1u) % 64u + 1u;  // bits of word wt at and below bit hv - 1
+        const u64 d = sm.diff[0] & (bits == 64u ? ~0ull : ((1ull << bits) - 1ull));
+        if (d == 0)
+            return false;
+        const u32 nhv = (hv - bits) + (64u - (u32)__clzll((long long)d));
+        if (nhv >= hv)
+            return false;  // the top bit varies already: the groups are duplicates
+        hv = nhv;
+        __syncthreads();
+    }
+    const u32 w0 = key_words - 1u - (hv - 1u) / 64u;  // words above it are equal inside the bin
+    auto code_of_rec = [&](u32 e) {
+        const u64 lw = recs[(u64)e * rw + cw.wl];
+        return window_of(cw, lw, cw.wh != cw.wl ? recs[(u64)e * rw + cw.wh] : lw);
+    };
+    // group starts: exclusive prefix of the counts (thread-contiguous codes)
+    const u32 PER = NC > THREADS ? NC / THREADS : 1u;
+    const u32 c0 = tid * PER;
+    const u32 nmine = c0 < NC ? PER : 0u;
+    u32 part = 0;
+    for (u32 i = 0; i < nmine; ++i)
+        part += cnt[c0 + i];
+    u32 incl = part;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 x = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= (u32)o)
+            incl += x;
+    }
+    if (lane == 31)
+        sm.rank.wsum[w] = incl;
+    __syncthreads();
+    u32 run = incl - part;
+    for (int i = 0; i < (int)w; ++i)
+        run += sm.rank.wsum[i];
+    for (u32 i = 0; i < nmine; ++i) {
+        const u32 c = cnt[c0 + i];
+        cnt[c0 + i] = run;
+        run += c;
+    }
+    __syncthreads();
+    // placement: afterwards cnt[c] is the end of group c (and the start of c + 1)
+    for (u32 e = tid; e < m; e += THREADS)
+        sm.xidx[atomicAdd(&cnt[code_of_rec(e)], 1u)] = (unsigned short)e;
+    __syncthreads();
+    // final place of every record inside its group
+    for (u32 s2 = tid; s2 < m; s2 += THREADS) {
+        const u32 e = sm.xidx[s2];
+        const u32 c = code_of_rec(e);
+        const u32 gs = c ? cnt[c - 1u] : 0u, ge = cnt[c];
+        u32 np = gs;
+        for (u32 j = gs; j < ge; ++j) {
+            if (j == s2)
+                continue;
+            const u32 f = sm.xidx[j];
+            const int cm = key_cmp(recs, rw, f, e, w0, key_words);
+            np += (cm < 0 || (cm == 0 && f < e)) ? 1u : 0u;
+        }
+        sm.xnew[np] = (unsigned short)e;
+    }
+    __syncthreads();
+    // one coalesced write in the final order
+    for (u32 s2 = tid; s2 < m; s2 += THREADS)
+        copy_record<RW>(out + (u64)s2 * rw, recs + (u64)sm.xnew[s2] * rw, rw);
+    return true;
 }
 
 // -------------------------------------------------------------- warp path
@@ -627,13 +788,21 @@ __device__ __forceinline__ void block_item(unsigned char *smem_raw, u64 *__restr
         // sub-bin boundaries: a run of one parent's sub-bins is grouped by the
         // parent's split digit p; a run of arrays takes them from the offsets
         const bool segs = (item.flags & ITEM_SEG) != 0;
-        const u32 p = item.digit;
-        const u32 p_word = segs ? 0u : key_words - 1u - p / 8u;
-        const u32 p_byte = segs ? 8u : p % 8u;  // bytes of p_word below the split digit that may vary
+        // a run of sub-bins: the parent split the key bits [lo, lo + pw); the
+        // sub-bins' values lie within 256 of the first record's
+        const u32 lo = item.digit, pw = item_w(item.flags);
+        const Window pwin = make_window(segs ? 64u * key_words : lo + pw, segs ? 1u : pw, key_words);
+        u32 p_word = segs ? 0u : pwin.wl, p_bits = segs ? 64u : pwin.sl;  // bits below the split that may vary
+        if (!segs && p_bits == 0) {
+            ++p_word;
+            p_bits = 64u;
+        }
         if (!segs) {
+            const u32 v0 = window_of(pwin, recs[pwin.wl], recs[pwin.wh]);
             for (u32 e0 = w * 32u; e0 < m; e0 += THREADS) {
                 const u32 e = e0 + lane;
-                const u32 d = e < m ? digit_of_word(recs[(u64)e * rw + p_word], 8u * p_byte) : (u32)RADIX;
+                const u32 d = e < m ? window_of(pwin, recs[(u64)e * rw + pwin.wl], recs[(u64)e * rw + pwin.wh]) - v0
+                                    : (u32)RADIX;
                 const u32 d0 = __shfl_sync(FULL_MASK, d, 0);
                 const u32 same = __ballot_sync(FULL_MASK, d == d0);
                 if (same == FULL_MASK) {
@@ -645,7 +814,7 @@ __device__ __forceinline__ void block_item(unsigned char *smem_raw, u64 *__restr
             }
         }
         // key digits below p that vary anywhere in the run
-        varying_digits_below<THREADS, K>(sm, recs, rw, m, p_word, p_byte, key_words);
+        varying_digits_below<THREADS, K>(sm, recs, rw, m, p_word, p_bits, key_words);
         if (segs) {
             // arrays [tile_base, tile_base + row) of the offset table (row <= 256)
             const u64 o0 = seg_off[item.tile_base];
@@ -684,14 +853,23 @@ __device__ __forceinline__ void block_item(unsigned char *smem_raw, u64 *__restr
                               sm.vshift, nv, p_word, key_words, out);
         }
     } else {
-        u32 id[K];
-        const u32 kv = (m + THREADS - 1) / THREADS;
-        block_path<THREADS, K>(sm, recs, rw, m, kv, item.digit, key_words, id);
+        bool done = false;
+        if constexpr (THREADS * K >= (int)CODE_N)
+            done = m > 1 && block_code_sort<THREADS, K, RW>(sm, recs, rw, m, item_hi(item.digit, item.flags),
+                                                            key_words, out);
+        if (!done) {
+            if (tid == 0)
+                sm.big_group = 0;
+            __syncthreads();
+            u32 id[K];
+            const u32 kv = (m + THREADS - 1) / THREADS;
+            block_path<THREADS, K>(sm, recs, rw, m, kv, item.digit, key_words, id);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
-            if ((u32)k < kv && pos < m)
-                copy_record<RW>(out + (u64)pos * rw, recs + (u64)id[k] * rw, rw);
+            for (int k = 0; k < K; ++k) {
+                const u32 pos = w * 32u * kv + (u32)k * 32u + lane;
+                if ((u32)k < kv && pos < m)
+                    copy_record<RW>(out + (u64)pos * rw, recs + (u64)id[k] * rw, rw);
+            }
         }
     }
     if (tid == 0)

@@ -56,79 +56,136 @@ __device__ void append_block(const PlanArgs &a, u64 begin, u64 count, u32 digit,
     a.blocks[slot] = it;
 }
 
-// Next digit below p that varies inside the bin, decided from the OR and AND of
-// the key word holding p (bytes where they differ vary).  Returns -1 when no
-// digit is left.  When the rest of this word is constant, the top digit of the
-// next word is returned: its own histogram will tell.
-__device__ int next_varying_digit(u32 p, u64 vor, u64 vand)
+// Digit a learned sub-bin splits on next: the model's low digit after its
+// top digit, the key's top byte after the model's low digit.
+__device__ __forceinline__ bool learned_child_grid(const PlanArgs &a, u32 p, u64 begin, u64 count, u32 flags)
 {
-    const u64 diff = vor ^ vand;
-    for (int b = (int)(p % 8u) - 1; b >= 0; --b)
-        if ((diff >> (8 * b)) & 0xffu)
-            return (int)(p - (p % 8u)) + b;
-    if (p < 8u)
-        return -1;
-    return (int)(p - (p % 8u)) - 1;
+    if (p == DIGIT_LEARNED_HI) {
+        append_grid_item(a, begin, count, DIGIT_LEARNED_LO,
+                         (flags & ~(ITEM_W_MASK | ITEM_C_MASK)) | (8u << ITEM_W_SHIFT), 8u);
+        return true;
+    }
+    append_bin(a, begin, count, a.top_digit, flags);
+    return true;
 }
 
-// Digit a sub-bin splits on next: the model's low digit after its top digit,
-// the key's top digit after the model's low digit, else the next key digit
-// down (-1 when none is left).
-__device__ __forceinline__ int child_digit(u32 p, u32 top)
+// The highest key bit below `lo` that may still vary inside a bin whose key
+// word `word` has OR `vor` and AND `vand` over its records, plus one (0: none
+// left).  Bits below lo inside that word are checked; when all of them are
+// constant, the next word's top is returned (its own histogram will tell).
+__device__ __forceinline__ u32 next_varying_hi(u32 lo, u64 vor, u64 vand)
 {
-    if (p == DIGIT_LEARNED_HI)
-        return (int)DIGIT_LEARNED_LO;
-    if (p == DIGIT_LEARNED_LO)
-        return (int)top;
-    return p > 0 ? (int)p - 1 : -1;
+    if (lo == 0)
+        return 0;
+    const u32 sl = lo % 64u;
+    if (sl == 0)
+        return lo;
+    const u64 diff = (vor ^ vand) & ((1ull << sl) - 1ull);
+    return diff ? (lo - sl) + (64u - (u32)__clzll((long long)diff)) : lo - sl;
 }
 
-__global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
+constexpr u32 PLAN_THREADS = 256;
+
+// Block-wide exclusive scan of one u64 per thread (PLAN_THREADS threads);
+// `total` gets the sum.  Contains barriers.
+__device__ __forceinline__ u64 plan_scan(u64 v, u64 &total, u64 *wsum)
 {
-    __shared__ u64 s_cnt[RADIX];
-    __shared__ u64 s_ex[RADIX];
-    __shared__ unsigned char s_big[RADIX];
-    __shared__ u64 s_wsum[RADIX / 32];
+    const u32 lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    u64 incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 x = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= (u32)o)
+            incl += x;
+    }
+    if (lane == 31)
+        wsum[w] = incl;
+    __syncthreads();
+    u64 add = 0, tot = 0;
+#pragma unroll
+    for (u32 i = 0; i < PLAN_THREADS / 32; ++i) {
+        add += i < w ? wsum[i] : 0ull;
+        tot += wsum[i];
+    }
+    total = tot;
+    __syncthreads();
+    return add + incl - v;
+}
+
+// One CTA per big bin of the level: its histogram is the inclusive counts its
+// last chunk published; the exclusive prefix of it (Sec. 1) gives every
+// sub-bin's start, written over those counts for the distribution kernel.
+// Then every sub-bin is sent where it belongs (see the file comment).
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
+{
+    __shared__ u64 s_wsum[PLAN_THREADS / 32];
+    __shared__ u64 s_key[KMAX];            // run key of every small sub-bin (~0: not small)
     __shared__ u32 s_slot, s_tb, s_nt;
-    const u32 d = threadIdx.x, lane = d & 31u, w = d >> 5;
+    __shared__ u64 s_blk;
+    __shared__ u32 s_err;
+    const u32 tid = threadIdx.x;
+    if (tid == 0)
+        s_err = ld_relaxed_u32(&a.ctrs->err);
+    __syncthreads();
+    if (s_err)
+        return;  // a histogram that failed (timeout) leaves nothing to plan
     const u32 n_grid = a.ctrs->grid_cur;
+    const u32 smallmax = a.cap_b / 2u < a.warp_bin ? a.cap_b / 2u : a.warp_bin;
+    const u64 run_target = a.cap_b - smallmax;
     for (u32 g = blockIdx.x; g < n_grid; g += gridDim.x) {
         const WorkItem it = a.grid_cur[g];
         const u32 p = it.digit;
         const bool learned = p >= DIGIT_LEARNED_HI;
-        const u64 h = a.hist[(u64)g * RADIX + d];
+        const u32 wb = learned ? 8u : item_w(it.flags);
+        const u32 K = 1u << wb;
+        const u32 hi = learned ? 0u : item_hi(p, it.flags);
+        const u32 lo = learned ? 0u : hi - wb;
+        const u32 nch = ceil_div_u64(it.count, a.tile_h);
+        u64 *row = a.status + a.cell_cur[g] + (u64)(nch - 1u) * K;
         if (p == DIGIT_LEARNED_LO && !a.ctrs->learned_ok) {
             // the learned partition failed its balance check: this bin goes on
             // with plain key digits (its top-8-bit model split stays valid)
-            if (d == 0)
+            if (tid == 0)
                 append_bin(a, it.begin, it.count, a.top_digit, it.flags);
             __syncthreads();
             continue;
         }
-        const int is_const = __syncthreads_or(h == it.count);
+        // this thread's values: [v0, v0 + nv)
+        const u32 per = K >= PLAN_THREADS ? K / PLAN_THREADS : 1u;
+        const u32 v0 = K >= PLAN_THREADS ? tid * per : tid;
+        const u32 nv = (K >= PLAN_THREADS || tid < K) ? per : 0u;
+        u64 part = 0;
+        bool cst = false;
+        for (u32 i = 0; i < nv; ++i) {
+            const u64 h = row[v0 + i] & LB_VAL_MASK;
+            part += h;
+            cst |= (h == it.count);
+        }
+        const int is_const = __syncthreads_or(cst);
+        const u64 vor = a.orand[2ull * g], vand = a.orand[2ull * g + 1];
+        // children skip the bits below the window that are constant in the whole bin
+        const u32 chi = learned ? 0u : next_varying_hi(lo, vor, vand);
         if (is_const && !a.single_pass) {
-            if (d == 0) {
-                const int np = learned ? child_digit(p, a.top_digit)
-                                       : next_varying_digit(p, a.orand[2ull * g], a.orand[2ull * g + 1]);
-                if (np >= 0) {
-                    if (!learned)
-                        atomicAdd(&a.ctrs->skipped, (u64)(p - (u32)np));
-                    append_bin(a, it.begin, it.count, (u32)np, it.flags);
+            // a constant digit: no data movement, the bin moves on
+            if (tid == 0) {
+                if (learned) {
+                    learned_child_grid(a, p, it.begin, it.count, it.flags);
                 } else {
-                    atomicAdd(&a.ctrs->skipped, (u64)(p + 1));
-                    if (it.flags & ITEM_IN_TMP)
+                    atomicAdd(&a.ctrs->skipped, (u64)(hi - chi));
+                    if (chi > 0)
+                        append_bin_hi(a, it.begin, it.count, chi, it.flags);
+                    else if (it.flags & ITEM_IN_TMP)
                         append_copy(a, it.begin, it.count);
                 }
             }
             __syncthreads();
             continue;
         }
-        // this bin is distributed on digit p in this level's pass
-        if (d == 0) {
+        // this bin is distributed in this level's pass, chunk by chunk
+        if (tid == 0) {
             const u32 slot = atomicAdd(&a.ctrs->scatter, 1u);
-            const u32 nt = ceil_div_u64(it.count, a.tile_s);
-            const u32 tb = atomicAdd(&a.ctrs->scatter_tiles, nt);
-            if (slot >= a.caps.grid || (u64)tb + nt > a.caps.scat_tiles) {
+            const u32 tb = atomicAdd(&a.ctrs->scatter_tiles, nch);
+            if (slot >= a.caps.grid || (u64)tb + nch > a.caps.scat_tiles) {
                 set_error(a.ctrs, ST_INTERNAL);
                 s_nt = 0;
             } else {
@@ -136,87 +193,137 @@ __global__ void __launch_bounds__(RADIX) plan_kernel(PlanArgs a)
                 sc.tile_base = tb;
                 sc.row = g;
                 a.scat[slot] = sc;
-                s_nt = nt;
+                s_nt = nch;
             }
             s_slot = slot;
             s_tb = tb;
         }
         // exclusive prefix of the histogram: the start of every sub-bin (Sec. 1)
-        u64 incl = h;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const u64 v = __shfl_up_sync(FULL_MASK, incl, o);
-            if (lane >= (u32)o)
-                incl += v;
+        u64 total = 0;
+        u64 run = it.begin + plan_scan(part, total, s_wsum);
+        for (u32 i = 0; i < nv; ++i) {
+            const u64 h = row[v0 + i] & LB_VAL_MASK;
+            row[v0 + i] = run;  // the row becomes the sub-bin starts
+            run += h;
         }
-        if (lane == 31)
-            s_wsum[w] = incl;
-        __syncthreads();
-        u64 add = 0;
-        for (u32 i = 0; i < w; ++i)
-            add += s_wsum[i];
-        const u64 ex = add + incl - h;
-        a.hist[(u64)g * RADIX + d] = it.begin + ex;  // row becomes the digit bases
-        s_cnt[d] = h;
-        s_ex[d] = it.begin + ex;
-        __syncthreads();
-        for (u32 j = d; j < s_nt; j += RADIX)
-            a.tile_scat[s_tb + j] = s_slot;
+        for (u32 jj = tid; jj < s_nt; jj += PLAN_THREADS)
+            a.tile_scat[s_tb + jj] = s_slot;
         if (a.single_pass) {
             __syncthreads();
             continue;
         }
         const u32 cflags = it.flags ^ ITEM_IN_TMP;
-        const bool big = h > a.cap_b;
-        const int cd = child_digit(p, a.top_digit);
-        s_big[d] = big ? 1 : 0;
-        if (big) {
-            if (cd >= 0)
-                append_bin(a, it.begin + ex, h, (u32)cd, cflags);
-            else if (cflags & ITEM_IN_TMP)
-                append_copy(a, it.begin + ex, h);
+        const bool to_in = (cflags & ITEM_IN_TMP) != 0;  // children sit in tmp and must come back
+        const u64 end = it.begin + it.count;
+        if (!learned && chi == 0) {
+            // no key bit left that varies: every sub-bin is final, only to move back
+            if (tid == 0 && to_in)
+                append_copy(a, it.begin, it.count);
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();  // every start is written
+        auto start_of = [&](u32 c) { return c < K ? row[c] : end; };
+        // big sub-bins go on by themselves; small ones are counted into run keys
+        u64 kpart = 0;  // (non-small sub-bins << 48) | small records
+        for (u32 i = 0; i < nv; ++i) {
+            const u32 c = v0 + i;
+            const u64 b = start_of(c), h = start_of(c + 1) - b;
+            if (h > a.cap_b) {
+                if (learned)
+                    learned_child_grid(a, p, b, h, cflags);
+                else
+                    append_bin_hi(a, b, h, chi, cflags);
+            }
+            const bool small = !learned && h <= smallmax;
+            kpart += small ? h : (1ull << 48);
+        }
+        u64 ktot = 0;
+        u64 kex = plan_scan(kpart, ktot, s_wsum);
+        for (u32 i = 0; i < nv; ++i) {
+            const u32 c = v0 + i;
+            const u64 h = start_of(c + 1) - start_of(c);
+            const bool small = !learned && h <= smallmax;
+            s_key[c] = small ? (((kex >> 48) << 40) | (((kex & ((1ull << 48) - 1ull)) / run_target) << 8) |
+                                (u64)(c >> 8))
+                             : ~0ull;
+            kex += small ? h : (1ull << 48);
         }
         __syncthreads();
-        if (d == 0 && learned) {
-            // sub-bins of a model split share no known key digit: each is sorted on
-            // its own by the whole key
-            for (u32 c = 0; c < RADIX; ++c)
-                if (!s_big[c] && s_cnt[c] > 0)
-                    append_block(a, s_ex[c], s_cnt[c], a.top_digit, cflags);
-        } else if (d == 0) {
-            // small sub-bins: up to WARP_BIN records -> packed into runs of at most
-            // cap_b records (one warp per sub-bin); bigger ones -> one item each
-            const u32 cdigit = cd >= 0 ? (u32)cd : 0u;
-            u64 acc_b = 0, acc_n = 0;
-            for (u32 c = 0; c < RADIX; ++c) {
-                const u64 n = s_cnt[c];
-                if (s_big[c] || n > a.warp_bin) {
-                    if (acc_n)
-                        append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
-                    acc_n = 0;
-                    if (!s_big[c])
-                        append_block(a, s_ex[c], n, cdigit, cflags);
-                    continue;
-                }
-                if (n == 0)
-                    continue;
-                if (acc_n && acc_n + n > a.cap_b) {
-                    append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
-                    acc_n = 0;
-                }
-                if (acc_n == 0)
-                    acc_b = s_ex[c];
-                acc_n += n;
+        // on-chip items: runs of small sub-bins (one per run head) and single
+        // sub-bins up to cap_b records; one reservation per bin
+        auto is_head = [&](u32 c) {
+            return s_key[c] != ~0ull && (c == 0 || s_key[c - 1] != s_key[c]);
+        };
+        auto run_end = [&](u32 c) {
+            u32 e = c + 1;
+            while (e < K && s_key[e] == s_key[c])
+                ++e;
+            return e;
+        };
+        auto single = [&](u64 h) { return h > 1 && h <= a.cap_b && (learned || h > smallmax); };
+        u64 nitems = 0;
+        for (u32 i = 0; i < nv; ++i) {
+            const u32 c = v0 + i;
+            const u64 b = start_of(c), h = start_of(c + 1) - b;
+            if (is_head(c)) {
+                const u64 rc = start_of(run_end(c)) - b;
+                nitems += (rc > 1 || (rc == 1 && to_in)) ? 1u : 0u;
+            } else if (single(h)) {
+                nitems += 1;
             }
-            if (acc_n)
-                append_block(a, acc_b, acc_n, p, cflags | ITEM_RUN);
+        }
+        u64 ntot = 0;
+        u64 nex = plan_scan(nitems, ntot, s_wsum);
+        if (tid == 0)
+            s_blk = ntot ? atomicAdd(&a.ctrs->block, ntot) : 0ull;
+        __syncthreads();
+        if (s_blk + ntot > a.caps.block) {
+            if (tid == 0)
+                set_error(a.ctrs, ST_INTERNAL);
+            __syncthreads();
+            continue;
+        }
+        u64 slot = s_blk + nex;
+        for (u32 i = 0; i < nv; ++i) {
+            const u32 c = v0 + i;
+            const u64 b = start_of(c), h = start_of(c + 1) - b;
+            WorkItem bi;
+            bi.tile_base = 0;
+            bi.row = 0;
+            if (is_head(c)) {
+                const u64 rc = start_of(run_end(c)) - b;
+                if (rc > 1 || (rc == 1 && to_in)) {
+                    bi.begin = b;
+                    bi.count = rc;
+                    bi.digit = lo;  // a run holds the parent's window
+                    bi.flags = (cflags & ~(ITEM_W_MASK | ITEM_C_MASK)) | ITEM_RUN | (wb << ITEM_W_SHIFT);
+                    a.blocks[slot++] = bi;
+                }
+            } else if (single(h)) {
+                bi.begin = b;
+                bi.count = h;
+                bi.flags = cflags & ~(ITEM_W_MASK | ITEM_C_MASK);
+                if (learned)
+                    bi.digit = a.top_digit;
+                else
+                    grid_pos(chi, 8u, bi.flags, bi.digit, bi.flags);  // exact top bit for the on-chip sort
+                a.blocks[slot++] = bi;
+            } else if (learned && h == 1 && to_in) {
+                append_copy(a, b, h);
+            }
         }
         __syncthreads();
     }
 }
 
+// The first level's work item: the whole input as one grid bin (with a digit
+// width picked for its size; wmax == 0: the byte `top` itself, for the single
+// step entry points and the learned first pass), one mid-size bin or one
+// on-chip item.
 __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top,
-                            u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max)
+                            u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, u64 *cell0,
+                            u32 leaf, u32 wmax)
 {
     const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     const bool mid = !force_grid && n > cap_b && n <= bucket_max;
@@ -229,10 +336,18 @@ __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u
             bucket0[0] = it;
             c.bucket_cur = 1;
         } else if (grid) {
-            WorkItem it = {0ull, n, top, 0u, 0u, 0u};
+            WorkItem it = {0ull, n, top, 8u << ITEM_W_SHIFT, 0u, 0u};
+            u32 w = 8;
+            if (top < DIGIT_LEARNED_HI && wmax > 0) {
+                w = pick_width(n, 8u * top + 8u, leaf, wmax);
+                grid_pos(8u * top + 8u, w, 0u, it.digit, it.flags);
+            }
             grid0[0] = it;
+            if (cell0)
+                cell0[0] = 0;
             c.grid_cur = 1;
             c.grid_cur_tiles = nt;
+            c.cells_cur = (u64)nt << w;
         } else if (n > 1) {
             WorkItem it = {0ull, n, top, 0u, 0u, 0u};
             blocks[0] = it;
@@ -244,11 +359,11 @@ __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u
         tile_hist[j] = 0;
 }
 
-__global__ void prep_kernel(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs)
+__global__ void prep_kernel(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 zero_rows)
 {
     const u64 rows = ctrs->grid_cur;
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows * RADIX; i += stride) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; zero_rows && i < rows * RADIX; i += stride) {
         hist[i] = 0;
         dlight[i] = 0;
     }
@@ -265,6 +380,8 @@ __global__ void advance_kernel(Counters *c)
         c->grid_passes += 1;
     c->grid_cur = c->grid_next;
     c->grid_cur_tiles = c->grid_next_tiles;
+    c->cells_cur = c->cells_next;
+    c->cells_next = 0;
     c->grid_next = 0;
     c->grid_next_tiles = 0;
     c->scatter = 0;
@@ -284,6 +401,8 @@ copy_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *_
             const u32 *__restrict__ tile_copy, Counters *__restrict__ ctrs, u32 tile_c, u32 rw)
 {
     __shared__ u32 s_tile;
+    if (cta_failed(ctrs))
+        return;
     const u32 n_tiles = ctrs->copy_tiles;
     for (;;) {
         if (threadIdx.x == 0)
@@ -328,7 +447,8 @@ __global__ void batched_validate_kernel(const u64 *__restrict__ off, u32 n_segs,
 // most 256 arrays), sorted one warp per array.
 __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs, WorkItem *grid0, WorkItem *blocks,
                                         u32 *tile_hist, Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 warp_bin,
-                                        u32 tile_h, u32 win, WorkItem *bucket0, u32 bucket_max)
+                                        u32 tile_h, u32 win, WorkItem *bucket0, u32 bucket_max, u64 *cell0, u32 leaf,
+                                        u32 wmax)
 {
     if (ctrs->err)
         return;
@@ -349,12 +469,17 @@ __global__ void batched_classify_kernel(const u64 *__restrict__ off, u32 n_segs,
             const u32 slot = atomicAdd(&ctrs->grid_cur, 1u);
             const u32 nt = (u32)((c + tile_h - 1) / tile_h);
             const u32 tb = atomicAdd(&ctrs->grid_cur_tiles, nt);
-            if (slot >= caps.grid || (u64)tb + nt > caps.hist_tiles) {
+            const u32 w = pick_width(c, 8u * top + 8u, leaf, wmax);
+            const u64 cells = (u64)nt << w;
+            const u64 co = atomicAdd(&ctrs->cells_cur, cells);
+            if (slot >= caps.grid || (u64)tb + nt > caps.hist_tiles || co + cells > caps.cells) {
                 set_error(ctrs, ST_INTERNAL);
                 continue;
             }
             WorkItem it = {a, c, top, 0u, tb, slot};
+            grid_pos(8u * top + 8u, w, 0u, it.digit, it.flags);
             grid0[slot] = it;
+            cell0[slot] = co;
             for (u32 t = 0; t < nt; ++t)
                 tile_hist[tb + t] = slot;
         } else if (c > warp_bin) {
@@ -398,13 +523,14 @@ cudaError_t launch_check_drained(Counters *ctrs, cudaStream_t st)
 
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
                                 Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
-                                u32 bucket_max, cudaStream_t st)
+                                u32 bucket_max, u64 *cell0, u32 leaf, u32 wmax, cudaStream_t st)
 {
     batched_reset_kernel<<<1, 1, 0, st>>>(ctrs);
     const u32 blocks_n = n_segs / 256 + 1 < 4096 ? n_segs / 256 + 1 : 4096;
     batched_validate_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, ctrs);
     batched_classify_kernel<<<blocks_n, 256, 0, st>>>(off, n_segs, grid0, blocks, tile_hist, ctrs, caps, top, cap_b,
-                                                      WARP_BIN, tile_h, cap_b - WARP_BIN, bucket0, bucket_max);
+                                                      WARP_BIN, tile_h, cap_b - WARP_BIN, bucket0, bucket_max, cell0,
+                                                      leaf, wmax);
     return cudaGetLastError();
 }
 
@@ -437,19 +563,21 @@ cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st)
 }
 
 cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist, u64 n, u32 top_digit,
-                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, cudaStream_t st)
+                        u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, u64 *cell0,
+                        u32 leaf, u32 wmax, cudaStream_t st)
 {
     init_kernel<<<256, 256, 0, st>>>(ctrs, grid0, blocks, tile_hist, n, top_digit, cap_b, tile_h, force_grid, bucket0,
-                                     bucket_max);
+                                     bucket_max, cell0, leaf, wmax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, cudaStream_t st)
+cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows,
+                        cudaStream_t st)
 {
-    u64 work = (u64)n_grid_hint * RADIX;
+    u64 work = (u64)n_grid_hint * (zero_rows ? RADIX : 1u);
     u64 want = (work + 255) / 256 + 1;
     u32 blocks = (u32)(want < 4096ull ? want : 4096ull);
-    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, dlight, ctrs);
+    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, dlight, ctrs, zero_rows);
     return cudaGetLastError();
 }
 
@@ -457,7 +585,7 @@ cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st)
 {
     // n_grid == 0: count unknown on the host (device-driven levels): a fixed grid loops
     u32 blocks = n_grid == 0 ? 1216u : (n_grid < 65535u ? n_grid : 65535u);
-    plan_kernel<<<blocks, RADIX, 0, st>>>(a);
+    plan_kernel<<<blocks, PLAN_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -5,8 +5,9 @@ Inputs are built so that every branch of that kernel runs: bins at the first
 and at later levels, runs of small sub-bins, single sub-bins sorted by the
 whole CTA, sub-bins too big for shared memory that go on to the next level,
 bins whose last digit is split (no digit left after it) from either buffer,
-and heavy duplicates.  The same inputs sorted with the path switched off
-(RADULS_BUCKET_MAX=0) must give the same bytes.
+and heavy duplicates (with 8-bit digits in every distribution pass, as the
+inputs are built around them).  The same inputs sorted with the path switched
+off (RADULS_BUCKET_MAX=0) must give the same bytes.
 """
 from __future__ import annotations
 
@@ -27,6 +28,19 @@ def _cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     lib()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _byte_digits():
+    """8-bit digits in every distribution pass, so that the bins these inputs
+    are built around (and the mid-size class) occur as described."""
+    old = os.environ.get("RADULS_WMAX")
+    os.environ["RADULS_WMAX"] = "8"
+    yield
+    if old is None:
+        del os.environ["RADULS_WMAX"]
+    else:
+        os.environ["RADULS_WMAX"] = old
 
 
 def _set_byte(keys: np.ndarray, byte: int, values: np.ndarray) -> None:

@@ -29,7 +29,7 @@ def _cuda():
 def test_histogram_matches_oracle(oracle_mod, rec_bytes, key_bytes):
     import torch
     p = lib()
-    recs = datagen.random_records(3 * 16384 + 1234, rec_bytes, key_bytes, 5, alphabet=7)
+    recs = datagen.random_records(3 * 65536 + 1234, rec_bytes, key_bytes, 5, alphabet=7)
     d = to_dev(recs)
     for digit in sorted({0, 3, 7, 8 * key_bytes // 8 - 1, 8 * key_bytes // 8 - 5}):
         h = torch.zeros(256, dtype=torch.int64, device="cuda")
@@ -42,7 +42,7 @@ def test_histogram_matches_oracle(oracle_mod, rec_bytes, key_bytes):
 @pytest.mark.parametrize("alphabet", [3, None])
 def test_distribution_pass_matches_oracle(oracle_mod, rec_bytes, key_bytes, alphabet):
     p = lib()
-    n = 5 * 8192 + 333
+    n = 2 * 65536 + 5 * 8192 + 333      # several chunks (look-back), tiles within them, ragged tail
     recs = datagen.random_records(n, rec_bytes, key_bytes, 17 + rec_bytes, alphabet=alphabet)
     d = to_dev(recs)
     out = scratch(n, rec_bytes // 8)
@@ -128,11 +128,11 @@ def test_stats_report_passes(oracle_mod):
 
 
 def test_timeout_is_reported_and_context_survives(oracle_mod):
-    """A tile withholds its look-back counts: its successor's bounded wait runs
-    out, the pass reports RADULS_ERR_TIMEOUT, skips its writes, and the next
-    call on the same context works."""
+    """A histogram chunk withholds its look-back counts: its successor's bounded
+    wait runs out, the pass reports RADULS_ERR_TIMEOUT, skips its writes, and
+    the next call on the same context works."""
     p = lib()
-    n = 6 * 4096 + 100
+    n = 4 * 65536 + 100
     recs = datagen.random_records(n, 16, 8, 99)
     d = to_dev(recs)
     out = scratch(n, 2)
