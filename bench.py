@@ -76,6 +76,12 @@ WORKLOADS = {
     "batched16": dict(desc="200,000 arrays of 16 B records, sizes log-uniform on [16, 42324] (expected total "
                            "2^30), odd arrays with a fixed top half-key; one batched call (a per-array plain loop "
                            "on a prefix of the arrays timed alongside)", n=0, rec=16, key=8, mode="batched"),
+    "batched16w": dict(desc="about 11,400 arrays of 16 B records, sizes log-uniform on [16, 2^20] drawn until 2^30 "
+                            "records, odd arrays with a fixed top half-key; one batched call (a per-array plain loop "
+                            "timed alongside)", n=0, rec=16, key=8, mode="batched"),
+    "uniform64": dict(desc="2^27 records x 64 B (u64 key uniform, index, six payload words); key-index sort with one "
+                           "gather (the direct record sort timed alongside)", n=1 << 27, rec=64, key=8,
+                      mode="indexed"),
 }
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record
@@ -337,6 +343,8 @@ def compare_workload(name: str, pkg, steps: int, warmup: int, hbm_peak: float, p
     offsets = None
     if name == "batched16":
         host, offsets = datagen.batched16()
+    elif name == "batched16w":
+        host, offsets = datagen.batched16w()
     else:
         host = getattr(datagen, name)(w["n"])
     n = host.shape[0]
@@ -356,6 +364,9 @@ def compare_workload(name: str, pkg, steps: int, warmup: int, hbm_peak: float, p
     def form():
         if mode == "batched":
             pkg.raduls_sort_batched(recs, tmp, d_off, n_segs, rec, key)
+            return None
+        if mode == "indexed":
+            pkg.raduls_sort_indexed(recs, tmp, n, rec, key)
             return None
         return pkg.raduls_sort_ex(recs, tmp, n, rec, key, mode="learned", stats=True)
 
@@ -423,6 +434,8 @@ def compare_workload(name: str, pkg, steps: int, warmup: int, hbm_peak: float, p
     if mode == "batched":
         out["n_arrays"] = n_segs
         out["plain_form"] = f"every one of the {n_segs} arrays sorted by its own raduls_sort_ex call (plain mode)"
+    elif mode == "indexed":
+        out["plain_form"] = "the same input sorted record by record by raduls_sort_ex in plain mode"
     else:
         out["plain_form"] = "the same input sorted by raduls_sort_ex in plain mode"
         out["learned_used"] = f_st["learned_used"]
@@ -455,7 +468,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-tune", action="store_true", help="skip raduls_autotune before the warm-up")
-    ap.add_argument("--compare", default="skewed16,widekey32,batched16",
+    ap.add_argument("--compare", default="skewed16,widekey32,batched16,batched16w,uniform64",
                     help="workloads timed against the plain sort after the headline (N = 1 only; '' = none)")
     ap.add_argument("--compare-steps", type=int, default=3)
     args = ap.parse_args()

@@ -32,6 +32,11 @@ Workloads (sizes are the full ones; tests pass a smaller ``n``):
   [16, U] with U chosen so the expected total is 2^30; keys uniform; every odd
   array has its top 32 key bits fixed to mix(seed, array) >> 32.  Payload =
   index within the whole buffer.
+* ``batched16w`` -- the second batched reading: arrays with sizes log-uniform
+  on [16, 2^20], drawn until 2^30 records (about 11,400 arrays); keys as in
+  ``batched16``.
+* ``uniform64``  -- 2^27 records of 64 B: uniform u64 key, payload = index and
+  six uniform words (wide records, for the key-index sort).
 * ``widekey32``  -- 2^28 records of 32 B: key word 0 is one of 2^20 seeded
   distinct values drawn with Zipf(1.0) frequencies, key word 1 uniform;
   payload = (index, mix(seed, index)).
@@ -53,6 +58,8 @@ SEEDS = {
     "skewed16": 0x52414455_00000003,
     "batched16": 0x52414455_00000004,
     "widekey32": 0x52414455_00000005,
+    "batched16w": 0x52414455_00000006,
+    "uniform64": 0x52414455_00000007,
 }
 
 FULL_N = {
@@ -61,10 +68,11 @@ FULL_N = {
     "skewed16": 1 << 30,
     "batched16": 1 << 30,   # expected total; the array count is what is fixed
     "widekey32": 1 << 28,
+    "uniform64": 1 << 27,
 }
 
-REC_BYTES = {"uniform8": 8, "uniform16": 16, "skewed16": 16, "batched16": 16, "widekey32": 32}
-KEY_BYTES = {"uniform8": 8, "uniform16": 8, "skewed16": 8, "batched16": 8, "widekey32": 16}
+REC_BYTES = {"uniform8": 8, "uniform16": 16, "skewed16": 16, "batched16": 16, "widekey32": 32, "uniform64": 64}
+KEY_BYTES = {"uniform8": 8, "uniform16": 8, "skewed16": 8, "batched16": 8, "widekey32": 16, "uniform64": 8}
 
 BATCHED_N_ARRAYS = 200_000
 BATCHED_MIN = 16
@@ -131,6 +139,21 @@ def uniform16(n: int | None = None, seed: int | None = None, out: np.ndarray | N
     def fill(rng, lo, hi, o):
         o[lo:hi, 0] = rng.bit_generator.random_raw(hi - lo)
         o[lo:hi, 1] = np.arange(lo, hi, dtype=np.uint64)
+
+    return _chunked(n, seed, fill, out)
+
+
+def uniform64(n: int | None = None, seed: int | None = None) -> np.ndarray:
+    """Wide records: 64 B each, a uniform u64 key, the index, then six
+    uniform payload words."""
+    n = FULL_N["uniform64"] if n is None else n
+    seed = SEEDS["uniform64"] if seed is None else seed
+    out = np.empty((n, 8), dtype=np.uint64)
+
+    def fill(rng, lo, hi, o):
+        o[lo:hi, 0] = rng.bit_generator.random_raw(hi - lo)
+        o[lo:hi, 1] = np.arange(lo, hi, dtype=np.uint64)
+        o[lo:hi, 2:] = rng.bit_generator.random_raw((hi - lo) * 6).reshape(hi - lo, 6)
 
     return _chunked(n, seed, fill, out)
 
@@ -220,6 +243,40 @@ def batched16(n_arrays: int = BATCHED_N_ARRAYS, seed: int | None = None,
     return out, offsets
 
 
+BATCHED_WIDE_MAX = 1 << 20
+BATCHED_WIDE_TOTAL = 1 << 30
+
+
+def batched_sizes_wide(seed: int | None = None, total: int = BATCHED_WIDE_TOTAL) -> np.ndarray:
+    """Array sizes of the second batched reading: log-uniform on [16, 2^20],
+    drawn until their sum first reaches `total` (2^30 records: about 11,400
+    arrays, the biggest ones far above the mid-size class)."""
+    seed = SEEDS["batched16w"] if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x5A5A))
+    out, acc = [], 0
+    while acc < total:
+        u = rng.uniform(math.log(BATCHED_MIN), math.log(BATCHED_WIDE_MAX), size=1024)
+        sz = np.floor(np.exp(u)).astype(np.int64)
+        cs = acc + np.cumsum(sz)
+        k = int(np.searchsorted(cs, total, side="left"))
+        if k < sz.size:
+            out.append(sz[: k + 1])
+            acc = int(cs[k])
+            break
+        out.append(sz)
+        acc = int(cs[-1])
+    return np.concatenate(out)
+
+
+def batched16w(sizes: np.ndarray | None = None, seed: int | None = None):
+    """The second batched reading (sizes from batched_sizes_wide), keys drawn
+    as in batched16.  Returns (records, offsets)."""
+    seed = SEEDS["batched16w"] if seed is None else seed
+    if sizes is None:
+        sizes = batched_sizes_wide(seed)
+    return batched16(seed=seed, sizes=sizes)
+
+
 ZIPF_S5 = 1.0
 DISTINCT5 = 1 << 20
 
@@ -271,4 +328,5 @@ WORKLOADS = {
     "uniform16": uniform16,
     "skewed16": skewed16,
     "widekey32": widekey32,
+    "uniform64": uniform64,
 }

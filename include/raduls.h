@@ -133,6 +133,31 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
 int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                      const raduls_opts *opts, void *stream);
 
+/* The same result as raduls_sort(), reached through the keys alone: the
+ * records' keys are copied out with their positions as (key, index) pairs,
+ * the pairs are sorted (stable, so equal keys keep their index order), and
+ * the records are then moved once, by a gather into `tmp` in the pairs'
+ * order, and copied back into `in`.  Every distribution pass then moves
+ * key_bytes + 8 bytes per record instead of rec_bytes, which pays for wide
+ * records: the paper measures how its sort time grows with the record size
+ * (Sec. 4).  The pairs and their scratch (2 x n_recs x (key_bytes + 8) bytes)
+ * are held in the library's per-device workspace.  Conventions and errors as
+ * raduls_sort(). */
+int raduls_sort_indexed(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                        void *stream);
+
+/* Distinct keys of records already SORTED by their key, with the number of
+ * records holding each (the counting use of the sort, Sec. 5: k-mer
+ * counting): every run of equal keys of `in` becomes one entry.  Writes the
+ * runs' keys (key_bytes each, in key order) to d_keys_out, their lengths to
+ * d_counts_out and the number of runs to *d_n_unique (all DEVICE memory; the
+ * caller sizes d_keys_out for n_recs keys and d_counts_out for n_recs
+ * counts, the most there can be).  Pointers must be 8-byte aligned.  On
+ * unsorted input every maximal run of equal adjacent keys is counted as it
+ * stands.  Record shapes as raduls_sort(). */
+int raduls_unique_counts(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
+                         void *d_keys_out, uint64_t *d_counts_out, uint64_t *d_n_unique, void *stream);
+
 /* Sort n_segs independent arrays in one call.  Array s occupies records
  * [d_seg_offsets[s], d_seg_offsets[s+1]) of `in` (d_seg_offsets is a DEVICE
  * array of n_segs+1 non-decreasing u64 record offsets with d_seg_offsets[0]
@@ -277,10 +302,14 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
 /* Forget every tuned setting (back to the built-in shapes). */
 int raduls_autotune_reset(void);
 
-/* Test hook: make the next distribution pass withhold tile `tile`'s published
- * counts so that its successors' bounded waits run out (kind 1), or clear the
- * hook (kind 0).  The pass then reports RADULS_ERR_TIMEOUT through
- * raduls_stream_status() and skips its writes; the context stays usable. */
+/* Test hook: make the next distribution pass withhold the published counts
+ * of histogram chunk `tile` (65,536 records per chunk, numbered over the
+ * pass's bins) so that its successors' bounded look-back waits run out
+ * (kind 1); make the next batched call withhold the ready flag of pushed
+ * queue item number `tile` so that the persistent kernel's bounded wait for it
+ * runs out (kind 2); or clear the hooks (kind 0).  The call then reports
+ * RADULS_ERR_TIMEOUT through raduls_stream_status() and skips the rest of its
+ * work; the context stays usable. */
 int raduls_debug_inject(uint32_t kind, uint64_t tile);
 
 /* Device-side wait limit in nanoseconds for look-back spins (default 2e9). */

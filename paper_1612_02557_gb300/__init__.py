@@ -11,7 +11,8 @@ from __future__ import annotations
 from ._lib import (RaduLSError, RaduLSModel, STATUS, build_library, library_path, load, raduls_autotune,
                    raduls_autotune_reset, raduls_debug_inject, raduls_distribution_pass, raduls_histogram,
                    raduls_histogram_static, raduls_set_wait_limit_ns, raduls_sort, raduls_sort_batched, raduls_sort_ex,
-                   raduls_sort_host, raduls_status_string, raduls_stream_status)
+                   raduls_sort_host, raduls_sort_indexed, raduls_status_string, raduls_stream_status,
+                   raduls_unique_counts)
 
 __all__ = [
     "RaduLSError",
@@ -24,6 +25,8 @@ __all__ = [
     "raduls_sort_ex",
     "raduls_sort_batched",
     "raduls_sort_host",
+    "raduls_sort_indexed",
+    "raduls_unique_counts",
     "raduls_autotune",
     "raduls_autotune_reset",
     "raduls_histogram",

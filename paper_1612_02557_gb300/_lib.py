@@ -104,6 +104,8 @@ def load():
             "raduls_sort": [vp, vp, u64, u32, u32, vp],
             "raduls_sort_ex": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_sort_batched": [vp, vp, vp, u32, u32, u32, vp],
+            "raduls_sort_indexed": [vp, vp, u64, u32, u32, vp],
+            "raduls_unique_counts": [vp, u64, u32, u32, vp, vp, vp, vp],
             "raduls_sort_host": [vp, vp, u64, u32, u32, ctypes.POINTER(Opts), vp],
             "raduls_autotune": [vp, vp, u64, u32, u32, vp, u32, vp, vp],
             "raduls_autotune_reset": [],
@@ -243,6 +245,20 @@ def raduls_sort_batched(in_, tmp, seg_offsets, n_segs: int, rec_bytes: int, key_
     rc = load().raduls_sort_batched(_addr(in_), _addr(tmp), _addr(seg_offsets), n_segs, rec_bytes, key_bytes,
                                     _stream(stream, in_, tmp))
     _raise(rc, "raduls_sort_batched")
+
+
+def raduls_sort_indexed(in_, tmp, n_recs: int, rec_bytes: int, key_bytes: int, stream=None) -> None:
+    """Sort through (key, index) pairs, then one gather of whole records."""
+    rc = load().raduls_sort_indexed(_addr(in_), _addr(tmp), n_recs, rec_bytes, key_bytes, _stream(stream, in_, tmp))
+    _raise(rc, "raduls_sort_indexed")
+
+
+def raduls_unique_counts(in_, n_recs: int, rec_bytes: int, key_bytes: int, keys_out, counts_out, n_unique_out,
+                         stream=None) -> None:
+    """Distinct keys of sorted records with their counts (device outputs)."""
+    rc = load().raduls_unique_counts(_addr(in_), n_recs, rec_bytes, key_bytes, _addr(keys_out), _addr(counts_out),
+                                     _addr(n_unique_out), _stream(stream, in_))
+    _raise(rc, "raduls_unique_counts")
 
 
 class Tuning(ctypes.Structure):

@@ -674,6 +674,8 @@ __device__ __noinline__ void batched_split_call(unsigned char *smem_raw, u64 *in
         it.row = 0;
         q.dyn[slot] = it;
         __threadfence();
+        if (slot == *q.withhold)
+            return;  // test hook: the item stays unpublished, so its waiter's bounded wait runs out
         atomicExch(&q.ready[slot], 1u);
     };
     bucket_split_item<THREADS, K, KS, RW>(smem_raw, in, tmp, a, item, push);

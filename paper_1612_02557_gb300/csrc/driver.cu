@@ -187,12 +187,16 @@ struct Ctx {
     Work main, aux;
     ModelBufs mdl;
     DevBuf host_in, host_tmp;    // raduls_sort_host: the device copy of the records and its scratch
+    DevBuf pair_a, pair_b;       // raduls_sort_indexed: (key, index) pairs and their scratch
+    DevBuf rle;                  // raduls_unique_counts: per-tile run counts
+    u32 *withhold = nullptr;      // device word read by the batched kernel (dev_status + 16)
     cudaStream_t copy_st[COPY_STREAMS_MAX] = {};
     cudaEvent_t copy_ev[COPY_STREAMS_MAX + 1] = {};
     cudaEvent_t win_ev[BUCKET_WINDOWS_MAX] = {};
     bool have_copy = false;
     u64 wait_ns = 2000000000ull;
     u32 inject_tile = ~0u;
+    u32 withhold_dev = ~0u;       // the value last written to the device's withheld-slot word
     cudaEvent_t ev[1024] = {};
     bool have_events = false;
 };
@@ -202,6 +206,7 @@ Ctx g_ctx[MAX_DEVICES];
 std::mutex g_setting_mu;
 u64 g_wait_ns = 2000000000ull;
 u32 g_inject_tile = ~0u;
+u32 g_withhold_push = ~0u;  // pushed queue slot of the batched kernel whose ready flag is withheld
 
 cudaError_t ensure(DevBuf &b, size_t bytes, bool zero, bool *grew = nullptr, cudaStream_t st = 0)
 {
@@ -317,6 +322,11 @@ cudaError_t ctx_init(Ctx &c)
     e = cudaMemset(c.dev_status, 0, 256);
     if (e != cudaSuccess)
         return e;
+    c.withhold = c.dev_status + 16;
+    e = cudaMemset(c.withhold, 0xff, 4);
+    if (e != cudaSuccess)
+        return e;
+    c.withhold_dev = ~0u;
     c.inited = true;
     return cudaSuccess;
 }
@@ -848,6 +858,7 @@ struct BatchGraph {
     u32 n_segs = 0, rw = 0, kw = 0;
     int scat_var = -1;
     u32 cap_b = 0, bucket_max = 0, wmax = 0, leaf = 0;  // the shape the graph was captured with
+    u64 wait_ns = 0;
     void *ws[6] = {};  // workspace buffers the graph's kernels use (a regrown one forces a new capture)
 };
 
@@ -957,10 +968,21 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         q.dyn = (WorkItem *)(b + o_dyn);
         q.ready = (u32 *)(b + o_rdy);
         q.cap_dyn = (u32)cap_dyn;
+        q.withhold = c.withhold;
     }
+    u32 withhold = ~0u;
     {
         std::lock_guard<std::mutex> g(g_setting_mu);
         c.wait_ns = g_wait_ns;
+        withhold = g_withhold_push;
+        g_withhold_push = ~0u;  // one call only
+    }
+    if (withhold != c.withhold_dev) {
+        static thread_local u32 h_word;
+        h_word = withhold;
+        CK(cudaMemcpyAsync(c.withhold, &h_word, 4, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        c.withhold_dev = withhold;
     }
     BatchGraph &bg = g_batch[dev];
     void *const ws[6] = {wk.lists.p, wk.hist.p, wk.status.p, wk.tiles.p, wk.bscratch.p, wk.bqueue.p};
@@ -969,7 +991,8 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         same_ws = same_ws && bg.ws[i] == ws[i];
     const bool hit = bg.exec && bg.in == in && bg.tmp == tmp && bg.off == off && bg.n == n && bg.n_segs == n_segs &&
                      bg.rw == rw && bg.kw == kw && bg.in != nullptr && same_ws && bg.scat_var == s.scat_var &&
-                     bg.cap_b == s.cap_b && bg.bucket_max == s.bucket_max && bg.wmax == s.wmax && bg.leaf == s.leaf;
+                     bg.cap_b == s.cap_b && bg.bucket_max == s.bucket_max && bg.wmax == s.wmax && bg.leaf == s.leaf &&
+                     bg.wait_ns == c.wait_ns;
     if (!hit) {
         if (bg.exec) {
             cudaGraphExecDestroy(bg.exec);
@@ -1005,6 +1028,7 @@ int run_batched(Ctx &c, int dev, u64 *in, u64 *tmp, const u64 *off, u32 n_segs, 
         bg.bucket_max = s.bucket_max;
         bg.wmax = s.wmax;
         bg.leaf = s.leaf;
+        bg.wait_ns = c.wait_ns;
     }
     CK(cudaGraphLaunch(bg.exec, st));
     return RADULS_OK;
@@ -1092,6 +1116,75 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
 int raduls_sort(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, void *stream)
 {
     return raduls_sort_ex(in, tmp, n_recs, rec_bytes, key_bytes, nullptr, stream);
+}
+
+int raduls_sort_indexed(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, void *stream)
+{
+    int rc = check_args(in, tmp, n_recs, rec_bytes, key_bytes);
+    if (rc)
+        return rc;
+    if (n_recs <= 1)
+        return RADULS_OK;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaError_t e = ctx_init(*c);
+    if (e != cudaSuccess)
+        return to_status(e);
+    cudaStream_t st = (cudaStream_t)stream;
+    const u32 rw = rec_bytes / 8u, kw = key_bytes / 8u, pw = kw + 1u;
+    if (n_recs > (~0ull) / (pw * 8u))
+        return RADULS_ERR_INVALID_ARG;
+    const size_t pb = (size_t)n_recs * pw * 8u;
+    CK(ensure(c->pair_a, pb, false));
+    CK(ensure(c->pair_b, pb, false));
+    u64 *pa = (u64 *)c->pair_a.p, *pbuf = (u64 *)c->pair_b.p;
+    CK(launch_build_pairs((const u64 *)in, n_recs, rw, kw, pa, st));
+    SortJob j{};
+    j.in = pa;
+    j.tmp = pbuf;
+    j.n = n_recs;
+    j.rw = pw;
+    j.kw = kw;
+    j.mode = 1;
+    rc = run_sort(*c, c->main, j, st);
+    if (rc)
+        return rc;
+    CK(launch_gather((const u64 *)in, n_recs, rw, pa, pw, (u64 *)tmp, st));
+    CK(cudaMemcpyAsync(in, tmp, (size_t)n_recs * rec_bytes, cudaMemcpyDeviceToDevice, st));
+    return RADULS_OK;
+}
+
+int raduls_unique_counts(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes, void *d_keys_out,
+                         uint64_t *d_counts_out, uint64_t *d_n_unique, void *stream)
+{
+    if (rec_bytes % 8u || key_bytes % 8u || key_bytes < 8u || key_bytes > rec_bytes)
+        return RADULS_ERR_INVALID_ARG;
+    if (rec_bytes > 256u)
+        return RADULS_ERR_UNSUPPORTED;
+    if (!d_n_unique || (n_recs > 0 && (!in || !d_keys_out || !d_counts_out)))
+        return RADULS_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 7u) || ((uintptr_t)d_keys_out & 7u) || ((uintptr_t)d_counts_out & 7u) ||
+        ((uintptr_t)d_n_unique & 7u))
+        return RADULS_ERR_MISALIGNED;
+    if (n_recs > (1ull << 39))
+        return RADULS_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_recs == 0)
+        return to_status(cudaMemsetAsync(d_n_unique, 0, 8, st));
+    int rc = 0;
+    Ctx *c = current_ctx(&rc);
+    if (!c)
+        return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaError_t e = ctx_init(*c);
+    if (e != cudaSuccess)
+        return to_status(e);
+    CK(ensure(c->rle, rle_tiles(n_recs) * 8, false));
+    CK(launch_rle((const u64 *)in, n_recs, rec_bytes / 8u, key_bytes / 8u, (u64 *)c->rle.p, (u64 *)d_keys_out,
+                  (u64 *)d_counts_out, (u64 *)d_n_unique, st));
+    return RADULS_OK;
 }
 
 int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
@@ -1495,7 +1588,18 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
         }
     };
     float ms = 0.f;
+    // untimed sorts first: the GPU leaves its idle clocks and the workspace is
+    // allocated before anything is compared
+    {
+        const Tuned warm = best;
+        for (int i = 0; i < 3 && rc == RADULS_OK; ++i) {
+            time_one(warm, ms);
+            have_best = false;
+            timed = 0;
+        }
+    }
     time_one(best, ms);
+    const Tuned base_t = best;
     for (int v = 0; v < 9 && rc == RADULS_OK; ++v) {
         if (v == base.scat_var || !scatter_variant_fits(v, rw) || ((v == 3 || v == 4) && rw <= 4))
             continue;
@@ -1536,6 +1640,30 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
         if (t.bucket_max == best.bucket_max)
             continue;
         time_one(t, ms);
+    }
+    // the winner against the default once more, alternating, best of three
+    // each: the default stays unless the winner is clearly faster
+    if (rc == RADULS_OK && (best.scat_var != base_t.scat_var || best.wmax != base_t.wmax ||
+                            best.leaf != base_t.leaf || best.cap_b != base_t.cap_b ||
+                            best.bucket_max != base_t.bucket_max)) {
+        const Tuned win = best;
+        float mw = 1e30f, mb = 1e30f;
+        for (int i = 0; i < 3 && rc == RADULS_OK; ++i) {
+            float x = 0.f;
+            have_best = false;
+            time_one(win, x);
+            mw = x < mw ? x : mw;
+            have_best = false;
+            time_one(base_t, x);
+            mb = x < mb ? x : mb;
+        }
+        if (mw < mb * (1.f - TIE_FRAC)) {
+            best = win;
+            best_ms = mw;
+        } else {
+            best = base_t;
+            best_ms = mb;
+        }
     }
     g_force = nullptr;
     cudaEventDestroy(e0);
@@ -1685,6 +1813,10 @@ int raduls_debug_inject(uint32_t kind, uint64_t tile)
     }
     if (kind == 1 && tile < 0xffffffffull) {
         g_inject_tile = (u32)tile;
+        return RADULS_OK;
+    }
+    if (kind == 2 && tile < 0xffffffffull) {
+        g_withhold_push = (u32)tile;
         return RADULS_OK;
     }
     return RADULS_ERR_INVALID_ARG;

@@ -174,6 +174,7 @@ struct BatchQueue {
     WorkItem *dyn;
     u32 *ready;
     u32 cap_dyn;
+    const u32 *withhold;  // device word: the pushed slot whose ready flag is withheld (test hook; ~0u: none)
 };
 
 cudaError_t launch_batched_persistent(const Shape &s, u64 *in, u64 *tmp, const PlanArgs &a, const BatchQueue &q,
@@ -198,6 +199,13 @@ cudaError_t launch_check_drained(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_epoch_next(u32 *ep, u64 *status, u64 words, cudaStream_t st);
 cudaError_t launch_copy(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *copies, const u32 *tile_copy,
                         Counters *ctrs, cudaStream_t st);
+
+// Key-index sort and runs of equal keys (extras.cu).
+cudaError_t launch_build_pairs(const u64 *in, u64 n, u32 rw, u32 kw, u64 *pairs, cudaStream_t st);
+cudaError_t launch_gather(const u64 *in, u64 n, u32 rw, const u64 *pairs, u32 pw, u64 *out, cudaStream_t st);
+u64 rle_tiles(u64 n);
+cudaError_t launch_rle(const u64 *in, u64 n, u32 rw, u32 kw, u64 *tile_buf, u64 *keys, u64 *counts, u64 *n_runs,
+                       cudaStream_t st);
 
 // Learned model (learned.cu).
 cudaError_t lm_launch_sample(const u64 *in, u64 n, u32 rw, u32 S, u64 *out, cudaStream_t st);

@@ -69,6 +69,13 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.raduls_histogram_static(16, 10, 16, 8, 8, 4096, None) == 1   # digit out of range
     assert lib.raduls_histogram_static(8, 10, 16, 8, 7, 4096, None) == 2    # misaligned records
     assert lib.raduls_set_wait_limit_ns(0) == 1
+    # the key-index sort and the run counter: the same record rules, plus their own
+    assert lib.raduls_sort_indexed(16, 4096, 10, 12, 8, None) == 1     # rec_bytes not a multiple of 8
+    assert lib.raduls_sort_indexed(8, 4096, 10, 16, 8, None) == 2      # misaligned
+    assert lib.raduls_sort_indexed(0, 0, 1, 64, 8, None) == 0          # n <= 1 is a no-op
+    assert lib.raduls_unique_counts(8, 10, 16, 8, 8, 8, None, None) == 1   # no place for the run count
+    assert lib.raduls_unique_counts(4, 10, 16, 8, 8, 8, 8, None) == 2      # misaligned records
+    assert lib.raduls_unique_counts(8, 10, 16, 24, 8, 8, 8, None) == 1     # key longer than record
     # the host entry point: the same record rules, plus its own buffer rules
     assert lib.raduls_sort_host(16, 4096, 10, 12, 8, None, None) == 1   # rec_bytes not a multiple of 8
     assert lib.raduls_sort_host(None, 4096, 10, 16, 8, None, None) == 1  # no input

@@ -106,3 +106,18 @@ def test_shapes_match_the_bench_table(name):
     r = datagen.WORKLOADS[name](n)
     assert r.shape == (n, datagen.REC_BYTES[name] // 8)
     assert datagen.KEY_BYTES[name] <= datagen.REC_BYTES[name]
+
+
+def test_batched_wide_sizes_law():
+    """The second batched reading: log-uniform sizes on [16, 2^20] drawn until
+    their sum first reaches 2^30 (the last array crosses it)."""
+    sizes = datagen.batched_sizes_wide()
+    assert sizes.min() >= datagen.BATCHED_MIN and sizes.max() <= datagen.BATCHED_WIDE_MAX
+    total = int(sizes.sum())
+    assert total >= 1 << 30 and total - int(sizes[-1]) < 1 << 30
+    # mean of log-uniform [16, 2^20] is (2^20 - 16) / ln(2^16): about 94,547 -> about 11,360 arrays
+    mean = (datagen.BATCHED_WIDE_MAX - datagen.BATCHED_MIN) / math.log(datagen.BATCHED_WIDE_MAX / datagen.BATCHED_MIN)
+    assert abs(sizes.size * mean / (1 << 30) - 1.0) < 0.05
+    assert (sizes > 40_960).mean() > 0.25     # about 29% of the arrays lie above the mid-size class
+    recs, offs = datagen.batched16w(sizes=sizes[:40])
+    assert offs[-1] == recs.shape[0] and np.array_equal(np.diff(offs.astype(np.int64)), sizes[:40])

@@ -109,3 +109,51 @@ def test_pushed_sub_bins_and_heavy_groups(oracle_mod):
             k[lo:lo + 3000] = k[lo]
     recs[:, 0] = k
     _check(oracle_mod, recs, offs, 8, repeat=2)
+
+
+def test_wide_sizes_reading_prefix(oracle_mod):
+    """The second batched reading (sizes log-uniform on [16, 2^20]): its first
+    150 arrays, many of them far above the mid-size class."""
+    sizes = datagen.batched_sizes_wide()[:150]
+    recs, offs = datagen.batched16w(sizes=sizes)
+    _check(oracle_mod, recs, offs, 8)
+
+
+def _heavy_mid_arrays(count=6, size=40_000, seed=5):
+    """Mid-size arrays whose keys take only two top-byte values and few values
+    below them: their code groups are too big, so the persistent kernel splits
+    them stably and pushes the sub-bins back onto its queue."""
+    rng = np.random.default_rng(seed)
+    recs = np.empty((count * size, 2), dtype=np.uint64)
+    recs[:, 0] = (rng.integers(0, 2, count * size).astype(np.uint64) << np.uint64(56)) | \
+        rng.integers(0, 1 << 40, count * size, dtype=np.uint64)
+    recs[:, 1] = np.arange(count * size, dtype=np.uint64)
+    offs = np.arange(count + 1, dtype=np.uint64) * np.uint64(size)
+    return recs, offs
+
+
+def test_queue_wait_timeout_is_reported_and_context_survives(oracle_mod):
+    """A host-side switch withholds the ready flag of the first item the
+    persistent kernel pushes back: the CTA that takes its queue slot waits for
+    it, the bounded wait runs out, the call reports RADULS_ERR_TIMEOUT, and the
+    next batched call on the same context is correct."""
+    import torch
+    p = lib()
+    recs, offs = _heavy_mid_arrays()
+    n = recs.shape[0]
+    d_off = torch.from_numpy(offs.view(np.int64)).cuda()
+    t = scratch(n, 2)
+    p.raduls_set_wait_limit_ns(200_000_000)
+    try:
+        p.raduls_debug_inject(2, 0)
+        d = to_dev(recs)
+        p.raduls_sort_batched(d, t, d_off, offs.size - 1, 16, 8)
+        assert p.raduls_stream_status() == 6
+        assert p.raduls_stream_status() == 0
+    finally:
+        p.raduls_debug_inject(0, 0)
+        p.raduls_set_wait_limit_ns(2_000_000_000)
+    d = to_dev(recs)
+    p.raduls_sort_batched(d, t, d_off, offs.size - 1, 16, 8)
+    assert p.raduls_stream_status() == 0
+    np.testing.assert_array_equal(from_dev(d, n, 2), oracle_mod.sort_segments(recs, 8, offs, threads=8))
