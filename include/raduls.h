@@ -102,9 +102,11 @@ typedef struct {
     uint32_t mode;                  /* 0 AUTO (currently the plain passes: the learned first
                                        partition is not yet faster on skewed keys), 1 PLAIN,
                                        2 LEARNED */
-    uint32_t learned_log2_buckets;  /* 12..16, 0 = chosen from n */
-    float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio; 0 = 4.0 */
-    uint32_t train_steps;           /* Adam steps per stage of the model fit; 0 = 16 */
+    uint32_t learned_log2_buckets;  /* buckets of the learned pass, log2: 8..10, 0 = 10 */
+    float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio
+                                       (over buckets whose key word 0 varies); 0 = 4.0 */
+    uint32_t train_steps;           /* Adam steps per stage of the model fit: 0 = 16, at most
+                                       4096; 0x80000000 = the warm start alone */
     raduls_stats *stats;            /* host pointer or NULL */
 } raduls_opts;
 
@@ -192,11 +194,18 @@ const char *raduls_status_string(int status);
  * on the GPU to the empirical CDF of a sorted key sample (mean squared error):
  * each stage is warm-started at the sample's CDF at its knots, then refined by
  * Adam steps, stage 1 first, then stage 2 on stage 1's output.
- * raduls_sort_ex(mode = LEARNED) builds one internally; these calls expose
- * the model for testing and inspection. */
+ * raduls_sort_ex(mode = LEARNED) builds one internally (B = 2^learned_log2_buckets,
+ * at most 1,024) after the top byte's histogram pass: one distribution pass
+ * then splits the records into the B buckets (stable, so equal keys keep their
+ * order), recording every bucket's smallest and largest key word 0; a bucket
+ * of one key value is finished there (one-word keys) or goes on from key word
+ * 1; the others are sorted by the plain passes.  When the largest bucket whose
+ * key varies holds more than fallback_ratio times n / B records, the learned
+ * split is not used and the plain passes sort the whole input.  These calls
+ * expose the model for testing and inspection. */
 typedef struct raduls_model raduls_model;
 
-/* Fit a model with 2^log2_buckets buckets (12..16) to the n_recs records at
+/* Fit a model with 2^log2_buckets buckets (8..16) to the n_recs records at
  * `in` (device): each stage is warm-started from the sample's CDF at its knots
  * and refined by train_steps Adam steps.  train_steps = 0 leaves both stages
  * linear (the untrained model); train_steps = 0x80000000 keeps the warm start

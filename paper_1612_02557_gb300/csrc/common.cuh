@@ -199,13 +199,12 @@ struct Caps {
 // interval is an exact shift and lam = remainder / 2^sh; stage 2 has m uniform
 // knots on [0, 1].  Heights are learned and non-decreasing (h_0 = 0,
 // h_{m-1} = 1); a trained stage 1 stretches dense key ranges over their share
-// of [0, 1], so stage 2's uniform knots resolve them.  A key's rank estimate is p = C_j + min(floor(u * R_j), R_j - 1)
-// and its bucket b = floor(p * B / n), B = 2^log2B; every step is monotone in
-// the key, so bucket order is key order.  The bucket id is used as two MSD
-// "digits": its top 8 bits and its low (log2B - 8) bits.
+// of [0, 1], so stage 2's uniform knots resolve them.  A key's rank estimate
+// is p = C_j + min(floor(u * R_j), R_j - 1) and its bucket b = floor(p * B / n),
+// B = 2^log2B; every step is monotone in the key, so bucket order is key
+// order.  The sort splits on the bucket id as one digit of log2B bits.
 
-constexpr u32 DIGIT_LEARNED_HI = 0x10000u;  // digit code: top 8 bits of the model bucket
-constexpr u32 DIGIT_LEARNED_LO = 0x10001u;  // digit code: low bits of the model bucket
+constexpr u32 DIGIT_LEARNED = 0x10000u;  // digit code: the model's bucket (log2B bits, in the item's width)
 
 struct ModelSeg {
     u64 base;     // stage 1: knot 0 as a 56-bit in-segment key offset
@@ -223,18 +222,18 @@ struct Model {
     u64 root_cnt[RADIX];
     u64 root_c[RADIX];
     const float *h;          // knot heights of both stages (device)
-    const u64 *heavy;        // sorted keys that alone fill >= 1 ideal bucket in the sample
+    u64 *bmin, *bmax;        // per bucket: smallest and largest key word 0 seen by the learned pass
+    const u64 *heavy;        // sorted sample keys that alone fill an ideal bucket's share of the sample
     u64 n;                   // records the model partitions
-    u32 log2b;               // log2 of the bucket count (12..16)
-    u32 lo_bits;             // log2b - 8
+    u32 log2b;               // log2 of the bucket count
     u32 n_heavy;
     float inv_n;             // 1 / n (first guess of the bucket division)
 };
 
-constexpr u32 HEAVY_MAX = 4096;  // heavy keys tracked for the balance check (the heaviest ones)
+constexpr u32 HEAVY_MAX = 1024;  // heavy keys: at most one per bucket of the sort's learned pass
 
-// Is `key` one of the model's heavy keys (binary search of a sorted list)?
-__device__ __forceinline__ bool is_heavy(const u64 *list, u32 n, u64 key)
+// Is `key` one of the sorted keys list[0, n) (binary search)?
+__device__ __forceinline__ bool in_sorted(const u64 *list, u32 n, u64 key)
 {
     u32 a = 0, b = n;
     while (a < b) {
@@ -325,41 +324,6 @@ __device__ __forceinline__ u32 model_bucket(const Model *__restrict__ M, u64 key
     while (b + 1u < nb && (u64)(b + 1u) * M->n <= pb)
         ++b;
     return b;
-}
-
-// Which digit a pass splits on: a key byte (word, shift) or a model digit.
-struct DigitSel {
-    u32 word;
-    u32 shift;
-    u32 learned;  // 0 key byte, 1 model bucket top bits, 2 model bucket low bits
-};
-
-__device__ __forceinline__ DigitSel digit_sel(u32 digit, u32 key_words)
-{
-    DigitSel s;
-    if (digit >= DIGIT_LEARNED_HI) {
-        s.word = 0;
-        s.shift = 0;
-        s.learned = digit - DIGIT_LEARNED_HI + 1u;
-    } else {
-        s.word = key_words - 1u - digit / 8u;
-        s.shift = 8u * (digit % 8u);
-        s.learned = 0;
-    }
-    return s;
-}
-
-__device__ __forceinline__ u32 digit_of_key(const DigitSel &s, u64 key_word, const Model *M)
-{
-    if (s.learned == 0)
-        return (u32)(key_word >> s.shift) & 0xffu;
-    const u32 b = model_bucket(M, key_word);
-    return s.learned == 1 ? (b >> M->lo_bits) : (b & ((1u << M->lo_bits) - 1u));
-}
-
-__device__ __forceinline__ u32 digit_of(const DigitSel &s, const u64 *rec, const Model *M)
-{
-    return digit_of_key(s, rec[s.word], M);
 }
 
 // Look-back status word: flag (2 bits) | epoch (22 bits) | value (40 bits).

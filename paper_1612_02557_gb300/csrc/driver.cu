@@ -20,6 +20,13 @@ namespace raduls {
 
 u32 block_cap_of(int var);
 
+// The distribution shape of a record width that takes digits of up to
+// WIDE_MAX bits (one CTA per SM): for a learned pass with that many buckets.
+int wide_scatter_variant(u32 rw)
+{
+    return rw == 1 ? 0 : rw == 2 ? 1 : rw == 4 ? 2 : rw <= 8 ? 3 : 4;
+}
+
 // Distribution variants that fit a record width (see WSCATTER_VARIANTS).
 bool scatter_variant_fits(int v, u32 rw)
 {
@@ -172,7 +179,10 @@ struct ModelBufs {
     Model *model = nullptr;
     float *h = nullptr, *theta = nullptr, *am = nullptr, *av = nullptr, *tot = nullptr;
     double *E = nullptr, *G = nullptr, *Z = nullptr, *loss = nullptr;
-    u64 *sample = nullptr, *sample_tmp = nullptr, *root = nullptr, *heavy = nullptr;
+    u64 *sample = nullptr, *sample_tmp = nullptr, *root = nullptr;
+    u64 *bmin = nullptr, *bmax = nullptr;  // the learned pass's key range per bucket
+    u64 *heavy = nullptr;                  // heavy keys of the sample (at most HEAVY_MAX)
+    u32 *load = nullptr;                   // bucket loads of the sample (balance check)
     u32 *seg_start = nullptr;
     u32 S = 0, k_extra = 0, max_knots = 0, n_params_cap = 0, steps_done = 0;
     u32 log2b = 0;
@@ -388,7 +398,7 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
 }
 
 struct LevelBufs {
-    u64 *hist, *orand, *dlight, *status;
+    u64 *hist, *orand, *status;
     u32 *tile_scat;
 };
 
@@ -397,13 +407,12 @@ struct LevelBufs {
 cudaError_t work_level(Work &wk, const Shape &s, u64 n, u32 n_grid, LevelBufs &B, Caps &caps, cudaStream_t st)
 {
     const u64 rows = (u64)n_grid + 1;
-    const size_t hb = align256(rows * RADIX * 8), ob = align256(rows * 16), db = rows * RADIX * 8;
-    cudaError_t e = ensure(wk.hist, hb + ob + db, false);
+    const size_t hb = align256(rows * RADIX * 8), ob = align256(rows * 16);
+    cudaError_t e = ensure(wk.hist, hb + ob, false);
     if (e != cudaSuccess)
         return e;
     B.hist = (u64 *)wk.hist.p;
     B.orand = (u64 *)((char *)wk.hist.p + hb);
-    B.dlight = (u64 *)((char *)wk.hist.p + hb + ob);
     bool grew = false;
     e = ensure(wk.status, caps.cells * 8, true, &grew, st);
     if (e != cudaSuccess)
@@ -541,7 +550,8 @@ cudaError_t model_bufs(ModelBufs &M, u32 S, u32 k_extra)
                  o_am = take(knots * 4), o_av = take(knots * 4), o_tot = take(2 * RADIX * 4), o_E = take(knots * 8),
                  o_G = take(knots * 8), o_Z = take(RADIX * 8), o_loss = take(8), o_s = take((size_t)S * 8),
                  o_st = take((size_t)S * 8), o_root = take(RADIX * 8), o_seg = take((RADIX + 1) * 4),
-                 o_heavy = take(HEAVY_MAX * 8);
+                 o_bmin = take(KMAX * 8), o_bmax = take(KMAX * 8), o_heavy = take(HEAVY_MAX * 8),
+                 o_load = take(KMAX * 4);
     cudaError_t e = ensure(M.buf, off, true);
     if (e != cudaSuccess)
         return e;
@@ -560,7 +570,10 @@ cudaError_t model_bufs(ModelBufs &M, u32 S, u32 k_extra)
     M.sample_tmp = (u64 *)(b + o_st);
     M.root = (u64 *)(b + o_root);
     M.seg_start = (u32 *)(b + o_seg);
+    M.bmin = (u64 *)(b + o_bmin);
+    M.bmax = (u64 *)(b + o_bmax);
     M.heavy = (u64 *)(b + o_heavy);
+    M.load = (u32 *)(b + o_load);
     M.S = S;
     M.k_extra = k_extra;
     M.max_knots = 2u + k_extra;
@@ -601,14 +614,14 @@ int model_fit(Ctx &c, ModelBufs &M, const u64 *in, u64 n, u32 rw, const u64 *roo
     if (rc)
         return rc;
     TIMED(RADULS_K_LEARNED, lm_launch_build(M.sample, S, k_extra, M.root, n, log2b, M.h, M.model, M.seg_start,
-                                            M.max_knots, st));
-    TIMED(RADULS_K_LEARNED, lm_launch_init(M.theta, M.am, M.av, M.n_params_cap, st));
+                                            M.max_knots, M.bmin, M.bmax, st));
     {
-        // a key filling at least an ideal bucket's worth of the sample cannot be
-        // balanced by any bucket map: it is left out of the balance ratio
-        const u64 thr = (u64)S >> log2b;
-        TIMED(RADULS_K_LEARNED, lm_launch_heavy(M.sample, S, (u32)(thr > 1 ? thr : 2), M.heavy, M.model, st));
+        // a key filling an ideal bucket's share of the sample cannot be split by
+        // any bucket map: it is left out of the balance check
+        const u32 thr = S >> log2b;
+        TIMED(RADULS_K_LEARNED, lm_launch_heavy(M.sample, S, thr > 1 ? thr : 2u, M.heavy, M.model, st));
     }
+    TIMED(RADULS_K_LEARNED, lm_launch_init(M.theta, M.am, M.av, M.n_params_cap, st));
     // stage 1 on its own, then stage 2 on stage 1's output: each warm-started
     // from the sample's CDF at its knots, then `steps` Adam steps (steps = 0
     // keeps both stages linear: the untrained model)
@@ -628,13 +641,8 @@ int model_fit(Ctx &c, ModelBufs &M, const u64 *in, u64 n, u32 rw, const u64 *roo
     return RADULS_OK;
 }
 
-u32 default_log2b(u64 n, u32 cap_b)
-{
-    u32 l = 12;
-    while (l < 16 && (n >> l) > cap_b)
-        ++l;
-    return l;
-}
+// Buckets of the learned pass: as many as one distribution pass splits into.
+u32 default_log2b() { return WIDE_MAX; }
 
 // ---------------------------------------------------------------- the sort
 
@@ -672,6 +680,7 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         g_inject_tile = ~0u;
     }
     bool learned = false;
+    u32 log2b = 0;
     float ratio_limit = j.fallback_ratio > 0.f ? j.fallback_ratio : 4.f;
     int cur = 0;
     const bool whole_mid = !step_api && j.n > s.cap_b && j.n <= bmax;
@@ -713,18 +722,17 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             a.caps = L.caps;  // the level's buffers fix the distribution tile capacity
             a.status = B.status;
             const Model *model = learned ? c.mdl.model : nullptr;
-            TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, (j.hist_out || learned) ? 1u : 0u, st));
+            TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, wk.ctrs, n_grid, j.hist_out ? 1u : 0u, st));
             if (j.hist_out) {
                 // histogram only (raduls_histogram): one traversal, counts per value
-                TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, B.dlight,
-                                                 wk.ctrs, model, st));
+                TIMED(RADULS_K_HIST, launch_hist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, B.hist, B.orand, wk.ctrs,
+                                                 st));
                 CK(cudaMemcpyAsync(j.hist_out, B.hist, RADIX * 8, cudaMemcpyDeviceToDevice, st));
                 break;
             }
             TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
             TIMED(RADULS_K_HIST, launch_whist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status,
-                                              B.orand, B.dlight, wk.ctrs, model, wk.epoch, c.wait_ns, c.inject_tile,
-                                              st));
+                                              B.orand, wk.ctrs, model, wk.epoch, c.wait_ns, c.inject_tile, st));
             c.inject_tile = ~0u;
             if (level == 0 && may_learn) {
                 // the first pass's digit histogram is the model's root; AUTO
@@ -735,30 +743,45 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
                     // the root bin's histogram of its top byte: its last chunk's counts
                     const u64 nch = (j.n + s.tile_h - 1) / s.tile_h;
                     TIMED(RADULS_K_SETUP, launch_status_counts(B.status + (nch - 1) * RADIX, B.hist, RADIX, st));
-                    const u32 log2b = j.log2b ? j.log2b : default_log2b(j.n, s.cap_b);
-                    int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, j.train_steps, st, rec);
+                    log2b = j.log2b ? j.log2b : default_log2b();
+                    const bool warm_only = (j.train_steps & 0x80000000u) != 0;
+                    int rc = model_fit(c, c.mdl, j.in, j.n, j.rw, B.hist, log2b, warm_only ? 1u : j.train_steps, st,
+                                       rec, warm_only);
                     if (rc)
                         return rc;
                     learned = true;
-                    // restart the level on the model's top digit
-                    TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n,
-                                                      DIGIT_LEARNED_HI, s.cap_b, s.tile_h, 1u, nullptr, 0u, L.cell[0],
-                                                      s.leaf, 0u, st));
-                    TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, n_grid, 1u, st));
-                    TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
-                    TIMED(RADULS_K_HIST, launch_whist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status,
-                                                      B.orand, B.dlight, wk.ctrs, c.mdl.model, wk.epoch, c.wait_ns,
-                                                      ~0u, st));
-                    model = c.mdl.model;
+                    // the balance check on the model's sample decides before any record moves
+                    TIMED(RADULS_K_LEARNED, lm_launch_ratio(c.mdl.model, c.mdl.sample, c.mdl.S, c.mdl.load, wk.ctrs,
+                                                            ratio_limit, st));
+                    CK(cudaMemcpyAsync(wk.h_ctrs, wk.ctrs, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    if (wk.h_ctrs->learned_ok) {
+                        // restart the level on the model's bucket: one digit of log2b bits
+                        TIMED(RADULS_K_SETUP, launch_init(wk.ctrs, L.grid[0], L.blocks, L.tile_hist, j.n,
+                                                          DIGIT_LEARNED, s.cap_b, s.tile_h, 1u, nullptr, 0u,
+                                                          L.cell[0], s.leaf, log2b, st));
+                        TIMED(RADULS_K_SETUP, launch_keep_learned(wk.ctrs, wk.h_ctrs->learned_ratio, st));
+                        TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, wk.ctrs, n_grid, 0u, st));
+                        TIMED(RADULS_K_LEARNED, lm_launch_minmax_reset(c.mdl.model, st));
+                        TIMED(RADULS_K_SETUP, launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
+                        TIMED(RADULS_K_HIST, launch_whist(s, j.in, j.tmp, L.grid[cur], L.tile_hist, L.cell[cur],
+                                                          B.status, B.orand, wk.ctrs, c.mdl.model, wk.epoch,
+                                                          c.wait_ns, ~0u, st));
+                        model = c.mdl.model;
+                    }
+                    // else: the plain passes go on from this level's histogram of the top byte
                 }
             }
-            if (learned && level == 1)
-                TIMED(RADULS_K_LEARNED, lm_launch_ratio(B.dlight, wk.ctrs, c.mdl.model, ratio_limit, st));
             a.hist = B.hist;
             a.orand = B.orand;
             a.tile_scat = B.tile_scat;
+            a.model = model;
             TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-            TIMED(RADULS_K_SCATTER, launch_wscatter(s, j.in, j.tmp, L.scat, B.tile_scat, L.cell[cur], B.status,
+            // the learned pass needs a distribution shape that takes 2^log2b values
+            Shape sl = s;
+            if (model && ((u64)1 << log2b) > wscatter_kmax_of(s.scat_var))
+                sl.scat_var = wide_scatter_variant(j.rw);
+            TIMED(RADULS_K_SCATTER, launch_wscatter(sl, j.in, j.tmp, L.scat, B.tile_scat, L.cell[cur], B.status,
                                                     wk.ctrs, model, c.wait_ns, st));
         }
         if (n_bkt > 0 && n_grid == 0 && j.hout && !wk.h_ctrs->block && !wk.h_ctrs->copy) {
@@ -873,10 +896,10 @@ int enqueue_batched(Ctx &c, Work &wk, const Shape &s, u64 *in, u64 *tmp, const u
     int cur = 0;
     const u32 levels = 8u * kw;
     for (u32 level = 0; level < levels; ++level) {
-        CK(launch_prep(B.hist, B.orand, B.dlight, wk.ctrs, L.caps.grid, 0u, st));
+        CK(launch_prep(B.hist, B.orand, wk.ctrs, L.caps.grid, 0u, st));
         CK(launch_epoch_next(wk.epoch, B.status, wk.status.bytes / 8, st));
-        CK(launch_whist(s, in, tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status, B.orand, B.dlight, wk.ctrs,
-                        nullptr, wk.epoch, c.wait_ns, ~0u, st));
+        CK(launch_whist(s, in, tmp, L.grid[cur], L.tile_hist, L.cell[cur], B.status, B.orand, wk.ctrs, nullptr,
+                        wk.epoch, c.wait_ns, ~0u, st));
         PlanArgs a{};
         a.grid_cur = L.grid[cur];
         a.grid_next = L.grid[cur ^ 1];
@@ -1086,7 +1109,9 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
         return rc;
     if (opts && opts->mode > 2u)
         return RADULS_ERR_INVALID_ARG;
-    if (opts && opts->learned_log2_buckets && (opts->learned_log2_buckets < 12u || opts->learned_log2_buckets > 16u))
+    if (opts && opts->learned_log2_buckets && (opts->learned_log2_buckets < 8u || opts->learned_log2_buckets > WIDE_MAX))
+        return RADULS_ERR_INVALID_ARG;
+    if (opts && opts->train_steps > 4096u && opts->train_steps != 0x80000000u)
         return RADULS_ERR_INVALID_ARG;
     if (opts && opts->stats)
         std::memset(opts->stats, 0, sizeof(raduls_stats));
@@ -1198,7 +1223,8 @@ int raduls_sort_host(const void *h_in, void *h_out, uint64_t n_recs, uint32_t re
     if (n_recs > (1ull << 39) || n_recs > (~0ull) / rec_bytes)
         return RADULS_ERR_UNSUPPORTED;
     if (opts && (opts->mode > 2u ||
-                 (opts->learned_log2_buckets && (opts->learned_log2_buckets < 12u || opts->learned_log2_buckets > 16u))))
+                 (opts->learned_log2_buckets && (opts->learned_log2_buckets < 8u || opts->learned_log2_buckets > WIDE_MAX)) ||
+                 (opts->train_steps > 4096u && opts->train_steps != 0x80000000u)))
         return RADULS_ERR_INVALID_ARG;
     const size_t bytes = (size_t)n_recs * rec_bytes;
     if (h_in != h_out && n_recs > 0) {
@@ -1302,7 +1328,7 @@ int raduls_model_fit(raduls_model **out, const void *in, uint64_t n_recs, uint32
     int rc = check_args(in, in, 0, rec_bytes, key_bytes);
     if (rc)
         return rc;
-    if (n_recs < 2 || !in || log2_buckets < 12u || log2_buckets > 16u)
+    if (n_recs < 2 || !in || log2_buckets < 8u || log2_buckets > 16u)
         return RADULS_ERR_INVALID_ARG;
     if ((uintptr_t)in & 15u)
         return RADULS_ERR_MISALIGNED;

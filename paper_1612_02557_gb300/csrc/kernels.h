@@ -28,9 +28,10 @@ u32 hist_grid(const Shape &s);
 u32 block_grid(const Shape &s);
 u32 copy_grid();
 
+// Histogram of a key byte over every bin of the grid list (the histogram-only
+// entry points): per-bin rows of 256 counts and the OR / AND of the key word.
 cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items,
-                        const u32 *tile_item, u64 *hist, u64 *orand, u64 *dlight, Counters *ctrs,
-                        const Model *model, cudaStream_t st);
+                        const u32 *tile_item, u64 *hist, u64 *orand, Counters *ctrs, cudaStream_t st);
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks,
                               Counters *ctrs, const u64 *seg_off, cudaStream_t st);
 
@@ -40,7 +41,7 @@ cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const Wor
 // of that value in the bin's chunks up to and including it), then a scatter in
 // which every CTA distributes whole chunks on its own.
 cudaError_t launch_whist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                         const u64 *cell_off, u64 *status, u64 *orand, u64 *dlight, Counters *ctrs, const Model *model,
+                         const u64 *cell_off, u64 *status, u64 *orand, Counters *ctrs, const Model *model,
                          const u32 *epoch, u64 wait_ns, u32 inject_chunk, cudaStream_t st);
 cudaError_t launch_wscatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *items, const u32 *tile_item,
                             const u64 *cell_off, const u64 *status, Counters *ctrs, const Model *model, u64 wait_ns,
@@ -85,6 +86,7 @@ struct PlanArgs {
     u64 *cell_next;           // same for the next grid list
     u32 leaf;                 // sub-bin size the digit widths aim at
     u32 wmax;                 // widest digit of a pass (bits)
+    const Model *model;       // the learned model of a learned pass (its buckets' key ranges)
 };
 
 // Position windows of the last mid-size level (an end-to-end sort copies each
@@ -184,11 +186,12 @@ cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *
                         u32 cap_b, u32 tile_h, u32 force_grid, WorkItem *bucket0, u32 bucket_max, u64 *cell0,
                         u32 leaf, u32 wmax, cudaStream_t st);
 // Clear the level's OR / AND words (and, zero_rows, its per-bin histogram rows
-// for the histogram-only traversal and the learned balance counts).
-cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows,
+// for the histogram-only traversal).
+cudaError_t launch_prep(u64 *hist, u64 *orand, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows,
                         cudaStream_t st);
 cudaError_t launch_plan(const PlanArgs &a, u32 n_grid, cudaStream_t st);
 cudaError_t launch_advance(Counters *ctrs, cudaStream_t st);
+cudaError_t launch_keep_learned(Counters *ctrs, float ratio, cudaStream_t st);
 cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
                                   u32 *wstart, cudaStream_t st);
 cudaError_t launch_bucket_window_reset(Counters *ctrs, cudaStream_t st);
@@ -210,7 +213,8 @@ cudaError_t launch_rle(const u64 *in, u64 n, u32 rw, u32 kw, u64 *tile_buf, u64 
 // Learned model (learned.cu).
 cudaError_t lm_launch_sample(const u64 *in, u64 n, u32 rw, u32 S, u64 *out, cudaStream_t st);
 cudaError_t lm_launch_build(const u64 *sample, u32 S, u32 k_extra, const u64 *root_hist, u64 n, u32 log2b,
-                            const float *h, Model *M, u32 *seg_start, u32 max_knots, cudaStream_t st);
+                            const float *h, Model *M, u32 *seg_start, u32 max_knots, u64 *bmin, u64 *bmax,
+                            cudaStream_t st);
 cudaError_t lm_launch_init(float *theta, float *am, float *av, u32 n_params, cudaStream_t st);
 cudaError_t lm_launch_step(const Model *M, u32 stage, float *theta, float *am, float *av, float *h, float *tot,
                            double *E, double *G, double *Z, double *loss, const u64 *sample, const u32 *seg_start,
@@ -219,8 +223,14 @@ cudaError_t lm_launch_warm(const Model *M, u32 stage, const u64 *sample, const u
                            cudaStream_t st);
 cudaError_t lm_launch_heights(const Model *M, const float *theta, float *h, float *tot, double *E, double *G,
                               double *Z, double *loss, cudaStream_t st);
-cudaError_t lm_launch_ratio(const u64 *dlight, Counters *ctrs, const Model *M, float limit, cudaStream_t st);
+// Heavy keys of the sorted sample (runs of at least thr equal keys).
 cudaError_t lm_launch_heavy(const u64 *sample, u32 S, u32 thr, u64 *heavy, Model *M, cudaStream_t st);
+// The balance check of a model on its sample: the largest bucket load of the
+// keys that are not heavy over the ideal S / B (load: KMAX u32 scratch).
+cudaError_t lm_launch_ratio(const Model *M, const u64 *sample, u32 S, u32 *load, Counters *ctrs, float limit,
+                            cudaStream_t st);
+// Every bucket's key range back to empty (before a learned pass).
+cudaError_t lm_launch_minmax_reset(const Model *M, cudaStream_t st);
 cudaError_t lm_launch_bucket(const Model *M, const u64 *keys, u64 n, u32 *out, cudaStream_t st);
 
 }  // namespace raduls

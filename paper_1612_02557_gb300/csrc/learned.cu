@@ -40,7 +40,8 @@ __global__ void lm_sample_kernel(const u64 *__restrict__ in, u64 n, u32 rw, u32 
 __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__ sample, u32 S, u32 k_extra,
                                                         const u64 *__restrict__ root_hist, u64 n, u32 log2b,
                                                         const float *h_dev, Model *__restrict__ M,
-                                                        u32 *__restrict__ seg_start, u32 max_knots)
+                                                        u32 *__restrict__ seg_start, u32 max_knots,
+                                                        u64 *__restrict__ bmin, u64 *__restrict__ bmax)
 {
     __shared__ u32 s_m[RADIX];
     __shared__ u32 s_m1[RADIX];
@@ -99,10 +100,11 @@ __global__ void __launch_bounds__(RADIX) lm_build_kernel(const u64 *__restrict__
             off += s_m[i];
         }
         M->h = h_dev;
+        M->bmin = bmin;
+        M->bmax = bmax;
         M->n = n;
         M->inv_n = 1.f / (float)n;
         M->log2b = log2b;
-        M->lo_bits = log2b - 8u;
     }
     __syncthreads();
     M->root_cnt[j] = s_c[j];
@@ -378,52 +380,39 @@ lm_update_kernel(const Model *__restrict__ M, u32 stage, float *__restrict__ the
     }
 }
 
-// ------------------------------------------------------------ heavy keys
+// ------------------------------------------------------------ balance check
 
-// One CTA of 1024 threads: in the sorted sample, every key whose run of equal
-// values is at least thr long (it alone fills that many ideal buckets' worth
-// of the sample) is appended, in key order, to the heavy list.  When more than
-// HEAVY_MAX keys qualify, thr is doubled until the heaviest fit.
+// Every bucket's key range back to empty, before a learned pass fills it.
+__global__ void lm_minmax_reset_kernel(const Model *__restrict__ M)
+{
+    const u32 nb = 1u << M->log2b;
+    for (u32 b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        M->bmin[b] = ~0ull;
+        M->bmax[b] = 0;
+    }
+}
+
+// Heavy keys: in the sorted sample, every key whose run of equal values is
+// at least thr long (it alone fills an ideal bucket's share of the sample; no
+// monotone map of the key can split it), in key order.  One CTA of 1024
+// threads; at most HEAVY_MAX keys (with thr >= S / B there are at most B).
 __global__ void __launch_bounds__(1024) lm_heavy_kernel(const u64 *__restrict__ sample, u32 S, u32 thr,
                                                        u64 *__restrict__ heavy, Model *__restrict__ M)
 {
     __shared__ u32 wcount[32];
     __shared__ u32 base;
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
-    if (thr < 1)
-        thr = 1;
-    auto is_heavy_start = [&](u32 s, u32 t, u64 &key) {
-        if (s >= S)
-            return false;
-        key = sample[s];
-        const bool start = (s == 0) || sample[s - 1] != key;
-        return start && s + t - 1 < S && sample[s + t - 1] == key;
-    };
-    // pass 1 (repeated): how many keys reach thr; raise thr until they fit
-    for (int round = 0; round < 32; ++round) {
-        if (tid == 0)
-            base = 0;
-        __syncthreads();
-        for (u32 s0 = 0; s0 < S; s0 += 1024) {
-            u64 key = 0;
-            const u32 bal = __ballot_sync(FULL_MASK, is_heavy_start(s0 + tid, thr, key));
-            if (lane == 0 && bal)
-                atomicAdd(&base, (u32)__popc(bal));
-        }
-        __syncthreads();
-        const u32 count = base;
-        __syncthreads();
-        if (count <= HEAVY_MAX || thr >= S)
-            break;
-        thr = thr * 2u;
-    }
-    // pass 2: the list, in key order
     if (tid == 0)
         base = 0;
     __syncthreads();
     for (u32 s0 = 0; s0 < S; s0 += 1024) {
+        const u32 s = s0 + tid;
+        bool hv = false;
         u64 key = 0;
-        const bool hv = is_heavy_start(s0 + tid, thr, key);
+        if (s < S) {
+            key = sample[s];
+            hv = (s == 0 || sample[s - 1] != key) && s + thr - 1 < S && sample[s + thr - 1] == key;
+        }
         const u32 bal = __ballot_sync(FULL_MASK, hv);
         if (lane == 0)
             wcount[w] = __popc(bal);
@@ -447,37 +436,40 @@ __global__ void __launch_bounds__(1024) lm_heavy_kernel(const u64 *__restrict__ 
     }
 }
 
-// ------------------------------------------------------------ balance check
+// Bucket loads on the sample: every sample key that is not heavy counts in
+// its bucket.
+__global__ void lm_sample_load_kernel(const Model *__restrict__ M, const u64 *__restrict__ sample, u32 S,
+                                      u32 *__restrict__ load)
+{
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+        const u64 key = sample[i];
+        if (!in_sorted(M->heavy, M->n_heavy, key))
+            atomicAdd(&load[model_bucket(M, key)], 1u);
+    }
+}
 
-// One CTA: over the sub-bins of the model's second split (rows x 256 digits),
-// the largest count of records whose key is not heavy, divided by the ideal
-// n / B (heavy keys cannot be split by any monotone key map; the plain passes
-// that follow finish them through the constant-digit skip).  Sets learned_ok
-// when the ratio is at most `limit`.
-__global__ void __launch_bounds__(RADIX) lm_ratio_kernel(const u64 *__restrict__ dlight,
+// One CTA: the balance check -- the largest bucket load over the ideal S / B
+// (heavy keys left out: they cannot be balanced by any map, and the sort
+// finishes buckets of one key value without further passes).  Sets
+// learned_ok when the ratio is at most `limit`.
+__global__ void __launch_bounds__(RADIX) lm_ratio_kernel(const u32 *__restrict__ load, u32 S,
                                                         Counters *__restrict__ ctrs, const Model *__restrict__ M,
                                                         float limit)
 {
-    __shared__ u64 s_max[RADIX / 32];
-    const u32 rows = ctrs->grid_cur;
-    u64 mx = 0;
-    for (u64 i = threadIdx.x; i < (u64)rows * RADIX; i += RADIX) {
-        const u64 c = dlight[i];
-        mx = c > mx ? c : mx;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const u64 v = __shfl_xor_sync(FULL_MASK, mx, o);
-        mx = v > mx ? v : mx;
-    }
+    __shared__ u32 s_max[RADIX / 32];
+    const u32 nb = 1u << M->log2b;
+    u32 mx = 0;
+    for (u32 b = threadIdx.x; b < nb; b += RADIX)
+        mx = load[b] > mx ? load[b] : mx;
+    mx = __reduce_max_sync(FULL_MASK, mx);
     if ((threadIdx.x & 31u) == 0)
         s_max[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < RADIX / 32; ++i)
             mx = s_max[i] > mx ? s_max[i] : mx;
-        const double ideal = (double)M->n / (double)(1u << M->log2b);
-        const float ratio = (float)((double)mx / (ideal > 0 ? ideal : 1.0));
+        const double ideal = (double)S / (double)nb;
+        const float ratio = (float)((double)mx / ideal);
         ctrs->learned_ratio = ratio;
         ctrs->learned_ok = ratio <= limit ? 1u : 0u;
         ctrs->learned_fell_back = ratio <= limit ? 0u : 1u;
@@ -501,9 +493,11 @@ cudaError_t lm_launch_sample(const u64 *in, u64 n, u32 rw, u32 S, u64 *out, cuda
 }
 
 cudaError_t lm_launch_build(const u64 *sample, u32 S, u32 k_extra, const u64 *root_hist, u64 n, u32 log2b,
-                            const float *h, Model *M, u32 *seg_start, u32 max_knots, cudaStream_t st)
+                            const float *h, Model *M, u32 *seg_start, u32 max_knots, u64 *bmin, u64 *bmax,
+                            cudaStream_t st)
 {
-    lm_build_kernel<<<1, RADIX, 0, st>>>(sample, S, k_extra, root_hist, n, log2b, h, M, seg_start, max_knots);
+    lm_build_kernel<<<1, RADIX, 0, st>>>(sample, S, k_extra, root_hist, n, log2b, h, M, seg_start, max_knots, bmin,
+                                         bmax);
     return cudaGetLastError();
 }
 
@@ -541,15 +535,27 @@ cudaError_t lm_launch_heights(const Model *M, const float *theta, float *h, floa
     return cudaGetLastError();
 }
 
-cudaError_t lm_launch_ratio(const u64 *dlight, Counters *ctrs, const Model *M, float limit, cudaStream_t st)
-{
-    lm_ratio_kernel<<<1, RADIX, 0, st>>>(dlight, ctrs, M, limit);
-    return cudaGetLastError();
-}
-
 cudaError_t lm_launch_heavy(const u64 *sample, u32 S, u32 thr, u64 *heavy, Model *M, cudaStream_t st)
 {
     lm_heavy_kernel<<<1, 1024, 0, st>>>(sample, S, thr, heavy, M);
+    return cudaGetLastError();
+}
+
+cudaError_t lm_launch_ratio(const Model *M, const u64 *sample, u32 S, u32 *load, Counters *ctrs, float limit,
+                            cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(load, 0, KMAX * 4, st);
+    if (e != cudaSuccess)
+        return e;
+    u32 blocks = (S + 255) / 256;
+    lm_sample_load_kernel<<<blocks < 1024 ? (blocks ? blocks : 1) : 1024, 256, 0, st>>>(M, sample, S, load);
+    lm_ratio_kernel<<<1, RADIX, 0, st>>>(load, S, ctrs, M, limit);
+    return cudaGetLastError();
+}
+
+cudaError_t lm_launch_minmax_reset(const Model *M, cudaStream_t st)
+{
+    lm_minmax_reset_kernel<<<64, 256, 0, st>>>(M);
     return cudaGetLastError();
 }
 

@@ -94,16 +94,15 @@ extern "C" int raduls_histogram_static(const void *in, uint64_t n_recs, uint32_t
     WorkItem *item = reinterpret_cast<WorkItem *>(base + OFF_ITEM);
     u64 *hist = reinterpret_cast<u64 *>(base + OFF_HIST);
     u64 *orand = reinterpret_cast<u64 *>(base + OFF_ORAND);
-    u64 *light = reinterpret_cast<u64 *>(base + OFF_LIGHT);
     u32 *tiles = reinterpret_cast<u32 *>(base + OFF_TILES);
     // every scratch field is rewritten before it is read: init writes the
     // counters, the work item and the tile map; prep zeroes the row
     cudaError_t e = launch_init(ctrs, item, item, tiles, n_recs, digit, s.cap_b, s.tile_h, 1u, nullptr, 0u, nullptr, 0u, 0u,
                                 st);
     if (e == cudaSuccess)
-        e = launch_prep(hist, orand, light, ctrs, 1u, 1u, st);
+        e = launch_prep(hist, orand, ctrs, 1u, 1u, st);
     if (e == cudaSuccess)
-        e = launch_hist(s, (const u64 *)in, (const u64 *)in, item, tiles, hist, orand, light, ctrs, nullptr, st);
+        e = launch_hist(s, (const u64 *)in, (const u64 *)in, item, tiles, hist, orand, ctrs, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_hist_out, hist, RADIX * 8, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {

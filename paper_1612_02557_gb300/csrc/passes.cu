@@ -12,28 +12,20 @@ template <int THREADS, int UNROLL>
 __global__ void __launch_bounds__(THREADS)
 hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ items,
             const u32 *__restrict__ tile_item, u64 *__restrict__ hist, u64 *__restrict__ orand,
-            u64 *__restrict__ dlight, Counters *__restrict__ ctrs, u32 tile_recs, u32 rw, u32 key_words,
-            const Model *__restrict__ model)
+            Counters *__restrict__ ctrs, u32 tile_recs, u32 rw, u32 key_words)
 {
     constexpr int NW = THREADS / 32;
     __shared__ u32 cnt[NW][RADIX + 1];
-    __shared__ u32 light[RADIX];         // records per digit whose key is not heavy (model low digit only)
     __shared__ u64 red_or[NW], red_and[NW];
     __shared__ u32 s_tile;
-    extern __shared__ u64 heavy[];       // the model's heavy keys (dynamic: HEAVY_MAX words with a model)
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     const u32 n_tiles = ctrs->grid_cur_tiles;
-    const u32 n_heavy = model ? model->n_heavy : 0u;
-    for (u32 i = tid; i < n_heavy; i += THREADS)
-        heavy[i] = model->heavy[i];
     for (u32 i = lane; i < RADIX + 1; i += 32)
         cnt[w][i] = 0;
-    if (tid < RADIX)
-        light[tid] = 0;
     // Counts, OR / AND and bytes accumulate over consecutive tiles of the same
     // bin and go to global memory when the bin changes (or at the end): the
     // tiles of one big bin would otherwise all hit the same few counters.
-    u32 cur_row = ~0u, cur_learned = 0;
+    u32 cur_row = ~0u;
     u64 vor = 0, vand = ~0ull, bytes = 0;
     for (;;) {
         if (tid == 0)
@@ -49,8 +41,6 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
                     s += cnt[ww][tid];
                 if (s)
                     atomicAdd(&hist[(u64)cur_row * RADIX + tid], (u64)s);
-                if (cur_learned == 2 && light[tid])
-                    atomicAdd(&dlight[(u64)cur_row * RADIX + tid], (u64)light[tid]);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -75,8 +65,6 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
             }
             for (u32 i = lane; i < RADIX + 1; i += 32)
                 cnt[w][i] = 0;
-            if (tid < RADIX)
-                light[tid] = 0;
             vor = 0;
             vand = ~0ull;
             bytes = 0;
@@ -89,26 +77,24 @@ hist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkI
         const u64 lo = item.begin + (u64)(t - item.tile_base) * tile_recs;
         const u64 hi = min(item.begin + item.count, lo + tile_recs);
         const u64 *src = (item.flags & ITEM_IN_TMP) ? tmp : in;
-        const DigitSel sel = digit_sel(item.digit, key_words);
-        cur_learned = sel.learned;
+        // digit p: byte p % 8 of key word W - 1 - p / 8
+        const u32 word = key_words - 1u - item.digit / 8u, sh = 8u * (item.digit % 8u);
         bytes += (hi - lo) * (u64)min(rw * 8u, 32u);
         for (u64 base = lo; base < hi; base += (u64)THREADS * UNROLL) {
             u64 key[UNROLL];
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const u64 i = base + (u64)u * THREADS + tid;
-                key[u] = i < hi ? __ldcs(src + i * rw + sel.word) : 0ull;
+                key[u] = i < hi ? __ldcs(src + i * rw + word) : 0ull;
             }
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
                 const u64 i = base + (u64)u * THREADS + tid;
                 const bool valid = i < hi;
-                const u32 d = valid ? digit_of_key(sel, key[u], model) : (u32)RADIX;
+                const u32 d = valid ? (u32)(key[u] >> sh) & 0xffu : (u32)RADIX;
                 if (valid) {
                     vor |= key[u];
                     vand &= key[u];
-                    if (sel.learned == 2 && !is_heavy(heavy, n_heavy, key[u]))
-                        atomicAdd(&light[d], 1u);
                 }
                 // one add for a warp whose lanes share a digit (skewed data), else one per lane
                 const u32 d0 = __shfl_sync(FULL_MASK, d, 0);
@@ -150,7 +136,7 @@ u32 hist_grid(const Shape &)
 }
 
 cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                        u64 *hist, u64 *orand, u64 *dlight, Counters *ctrs, const Model *model, cudaStream_t st)
+                        u64 *hist, u64 *orand, Counters *ctrs, cudaStream_t st)
 {
     static thread_local int cached_dev = -1;
     static thread_local u32 grid = 0;
@@ -160,16 +146,8 @@ cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const Wor
         grid = hist_grid(s);
         cached_dev = dev;
     }
-    const size_t dyn = model ? (size_t)HEAVY_MAX * 8 : 0;
-    if (model) {
-        const cudaError_t e = cudaFuncSetAttribute(hist_kernel<HIST_THREADS, HIST_UNROLL>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess)
-            return e;
-    }
-    hist_kernel<HIST_THREADS, HIST_UNROLL><<<grid, HIST_THREADS, dyn, st>>>(in, tmp, items, tile_item, hist, orand,
-                                                                           dlight, ctrs, s.tile_h, s.rw, s.key_words,
-                                                                           model);
+    hist_kernel<HIST_THREADS, HIST_UNROLL><<<grid, HIST_THREADS, 0, st>>>(in, tmp, items, tile_item, hist, orand, ctrs,
+                                                                         s.tile_h, s.rw, s.key_words);
     return cudaGetLastError();
 }
 

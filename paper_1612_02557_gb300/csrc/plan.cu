@@ -56,17 +56,27 @@ __device__ void append_block(const PlanArgs &a, u64 begin, u64 count, u32 digit,
     a.blocks[slot] = it;
 }
 
-// Digit a learned sub-bin splits on next: the model's low digit after its
-// top digit, the key's top byte after the model's low digit.
-__device__ __forceinline__ bool learned_child_grid(const PlanArgs &a, u32 p, u64 begin, u64 count, u32 flags)
+// A learned bucket whose key word 0 is the same for all its records: with a
+// one-word key its records are equal keys, already in their stable order.
+__device__ __forceinline__ bool bucket_single_key(const PlanArgs &a, u32 c)
 {
-    if (p == DIGIT_LEARNED_HI) {
-        append_grid_item(a, begin, count, DIGIT_LEARNED_LO,
-                         (flags & ~(ITEM_W_MASK | ITEM_C_MASK)) | (8u << ITEM_W_SHIFT), 8u);
-        return true;
+    return a.model && a.model->bmin[c] == a.model->bmax[c];
+}
+
+// A learned bucket of more than cap_b records: its key bytes share nothing
+// known, so it is sorted from the top of the key (its constant bits are
+// skipped by the next pass's histogram), or from key word 1 when its word 0
+// is one value; a one-word bucket of one value is finished.
+__device__ __forceinline__ void learned_child(const PlanArgs &a, u32 c, u64 begin, u64 count, u32 flags)
+{
+    if (bucket_single_key(a, c)) {
+        if (a.key_words > 1u)
+            append_bin_hi(a, begin, count, 64u * (a.key_words - 1u), flags);
+        else if (flags & ITEM_IN_TMP)
+            append_copy(a, begin, count);
+        return;
     }
     append_bin(a, begin, count, a.top_digit, flags);
-    return true;
 }
 
 // The highest key bit below `lo` that may still vary inside a bin whose key
@@ -135,16 +145,16 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
     for (u32 g = blockIdx.x; g < n_grid; g += gridDim.x) {
         const WorkItem it = a.grid_cur[g];
         const u32 p = it.digit;
-        const bool learned = p >= DIGIT_LEARNED_HI;
-        const u32 wb = learned ? 8u : item_w(it.flags);
+        const bool learned = p == DIGIT_LEARNED;
+        const u32 wb = item_w(it.flags);
         const u32 K = 1u << wb;
         const u32 hi = learned ? 0u : item_hi(p, it.flags);
         const u32 lo = learned ? 0u : hi - wb;
         const u32 nch = ceil_div_u64(it.count, a.tile_h);
         u64 *row = a.status + a.cell_cur[g] + (u64)(nch - 1u) * K;
-        if (p == DIGIT_LEARNED_LO && !a.ctrs->learned_ok) {
-            // the learned partition failed its balance check: this bin goes on
-            // with plain key digits (its top-8-bit model split stays valid)
+        if (learned && !a.ctrs->learned_ok) {
+            // the learned partition failed its balance check: the bin is not
+            // distributed on it and goes on with the plain key digits
             if (tid == 0)
                 append_bin(a, it.begin, it.count, a.top_digit, it.flags);
             __syncthreads();
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
             // a constant digit: no data movement, the bin moves on
             if (tid == 0) {
                 if (learned) {
-                    learned_child_grid(a, p, it.begin, it.count, it.flags);
+                    append_bin(a, it.begin, it.count, a.top_digit, it.flags);
                 } else {
                     atomicAdd(&a.ctrs->skipped, (u64)(hi - chi));
                     if (chi > 0)
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
             const u64 b = start_of(c), h = start_of(c + 1) - b;
             if (h > a.cap_b) {
                 if (learned)
-                    learned_child_grid(a, p, b, h, cflags);
+                    learned_child(a, c, b, h, cflags);
                 else
                     append_bin_hi(a, b, h, chi, cflags);
             }
@@ -261,6 +271,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
                 ++e;
             return e;
         };
+        // a small learned bucket of one key value (one-word keys) needs no sort
+        auto done_bucket = [&](u32 c) { return learned && a.key_words == 1u && bucket_single_key(a, c); };
         auto single = [&](u64 h) { return h > 1 && h <= a.cap_b && (learned || h > smallmax); };
         u64 nitems = 0;
         for (u32 i = 0; i < nv; ++i) {
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
             if (is_head(c)) {
                 const u64 rc = start_of(run_end(c)) - b;
                 nitems += (rc > 1 || (rc == 1 && to_in)) ? 1u : 0u;
-            } else if (single(h)) {
+            } else if (single(h) && !(h > 0 && done_bucket(c))) {
                 nitems += 1;
             }
         }
@@ -300,11 +312,16 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
                     bi.flags = (cflags & ~(ITEM_W_MASK | ITEM_C_MASK)) | ITEM_RUN | (wb << ITEM_W_SHIFT);
                     a.blocks[slot++] = bi;
                 }
+            } else if (h > 0 && h <= a.cap_b && done_bucket(c)) {
+                if (to_in)
+                    append_copy(a, b, h);
             } else if (single(h)) {
                 bi.begin = b;
                 bi.count = h;
                 bi.flags = cflags & ~(ITEM_W_MASK | ITEM_C_MASK);
-                if (learned)
+                if (learned && bucket_single_key(a, c))
+                    grid_pos(64u * (a.key_words - 1u), 8u, bi.flags, bi.digit, bi.flags);  // from key word 1
+                else if (learned)
                     bi.digit = a.top_digit;
                 else
                     grid_pos(chi, 8u, bi.flags, bi.digit, bi.flags);  // exact top bit for the on-chip sort
@@ -336,9 +353,10 @@ __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u
             bucket0[0] = it;
             c.bucket_cur = 1;
         } else if (grid) {
-            WorkItem it = {0ull, n, top, 8u << ITEM_W_SHIFT, 0u, 0u};
-            u32 w = 8;
-            if (top < DIGIT_LEARNED_HI && wmax > 0) {
+            // the learned digit takes wmax bits (log2 of the model's bucket count)
+            u32 w = (top == DIGIT_LEARNED && wmax > 0) ? wmax : 8u;
+            WorkItem it = {0ull, n, top, w << ITEM_W_SHIFT, 0u, 0u};
+            if (top != DIGIT_LEARNED && wmax > 0) {
                 w = pick_width(n, 8u * top + 8u, leaf, wmax);
                 grid_pos(8u * top + 8u, w, 0u, it.digit, it.flags);
             }
@@ -359,18 +377,31 @@ __global__ void init_kernel(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u
         tile_hist[j] = 0;
 }
 
-__global__ void prep_kernel(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 zero_rows)
+__global__ void prep_kernel(u64 *hist, u64 *orand, const Counters *ctrs, u32 zero_rows)
 {
     const u64 rows = ctrs->grid_cur;
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; zero_rows && i < rows * RADIX; i += stride) {
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; zero_rows && i < rows * RADIX; i += stride)
         hist[i] = 0;
-        dlight[i] = 0;
-    }
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
         orand[2 * i] = 0;
         orand[2 * i + 1] = ~0ull;
     }
+}
+
+// After the learned pass's restart (init clears the counters): its balance
+// check passed with this ratio.
+__global__ void keep_learned_kernel(Counters *c, float ratio)
+{
+    c->learned_ok = 1;
+    c->learned_fell_back = 0;
+    c->learned_ratio = ratio;
+}
+
+cudaError_t launch_keep_learned(Counters *ctrs, float ratio, cudaStream_t st)
+{
+    keep_learned_kernel<<<1, 1, 0, st>>>(ctrs, ratio);
+    return cudaGetLastError();
 }
 
 __global__ void advance_kernel(Counters *c)
@@ -571,13 +602,12 @@ cudaError_t launch_init(Counters *ctrs, WorkItem *grid0, WorkItem *blocks, u32 *
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep(u64 *hist, u64 *orand, u64 *dlight, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows,
-                        cudaStream_t st)
+cudaError_t launch_prep(u64 *hist, u64 *orand, const Counters *ctrs, u32 n_grid_hint, u32 zero_rows, cudaStream_t st)
 {
     u64 work = (u64)n_grid_hint * (zero_rows ? RADIX : 1u);
     u64 want = (work + 255) / 256 + 1;
     u32 blocks = (u32)(want < 4096ull ? want : 4096ull);
-    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, dlight, ctrs, zero_rows);
+    prep_kernel<<<blocks, 256, 0, st>>>(hist, orand, ctrs, zero_rows);
     return cudaGetLastError();
 }
 

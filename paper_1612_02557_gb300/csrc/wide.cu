@@ -20,39 +20,39 @@
 //   * wscatter_kernel gives each CTA whole chunks: the chunk's write cursors
 //     are the sub-bin starts plus the previous chunk's inclusive counts, so no
 //     CTA ever waits for another.  It streams the chunk through shared memory
-//     in tiles (bulk asynchronous copies, the next tile loading while this one
-//     is ranked), ranks each tile's records stably by digit -- digits wider
-//     than 8 bits in two counting rounds, low bits first -- regroups them so
-//     that every digit's records leave as one contiguous run (the role of the
-//     paper's write-combining buffers, Sec. 2, Sec. 3.2), and advances the
-//     cursors.
-// A digit is a window of up to 12 key bits (bits.h of common.cuh), so one
-// pass can split a bin 4,096 ways; the width of each bin's digit is picked
-// when the bin is planned.
+//     in tiles (bulk asynchronous copies; with two buffers the next tile loads
+//     while this one is ranked), ranks each tile's records stably by digit
+//     (one match instruction per record finds its peers in the warp, per-warp
+//     counters give ranks in element order), regroups them so that every
+//     digit's records leave as one contiguous run (the role of the paper's
+//     write-combining buffers, Sec. 2, Sec. 3.2), and advances the cursors.
+// A digit is a window of up to 10 key bits (the Window of common.cuh), or the
+// learned model's bucket, so one pass can split a bin 1,024 ways; the width
+// of each bin's digit is picked when the bin is planned.
 #include "kernels.h"
 
 namespace raduls {
 
 namespace {
 
-// The digit of an item: a window of key bits, or one of the learned model's
-// two digits (values < 256).
+// The digit of an item: a window of key bits, or the learned model's bucket
+// (values < 2^w, w = the item's width: log2 of the model's bucket count).
 struct ItemDigit {
     Window win;
-    u32 learned;  // 0: key window; 1: model bucket's top bits; 2: its low bits
+    u32 learned;  // 0: key window; 1: model bucket of key word 0
     u32 K;        // digit values
 };
 
 __device__ __forceinline__ ItemDigit item_digit(const WorkItem &it, u32 key_words)
 {
     ItemDigit r;
-    if (it.digit >= DIGIT_LEARNED_HI) {
-        r.learned = it.digit - DIGIT_LEARNED_HI + 1u;
+    if (it.digit == DIGIT_LEARNED) {
+        r.learned = 1;
         r.win.wl = 0;
         r.win.wh = 0;
         r.win.sl = 0;
-        r.win.w = 8;
-        r.K = RADIX;
+        r.win.w = item_w(it.flags);
+        r.K = 1u << r.win.w;
     } else {
         const u32 w = item_w(it.flags);
         r.learned = 0;
@@ -66,8 +66,7 @@ __device__ __forceinline__ u32 digit_from(const ItemDigit &g, u64 lw, u64 hw, co
 {
     if (g.learned == 0)
         return window_of(g.win, lw, hw);
-    const u32 b = model_bucket(M, lw);
-    return g.learned == 1 ? (b >> M->lo_bits) : (b & ((1u << M->lo_bits) - 1u));
+    return model_bucket(M, lw);
 }
 
 // Decoupled look-back for value d of chunk j > 0 of one bin, whose status
@@ -127,16 +126,14 @@ template <int THREADS, int UNROLL>
 __global__ void __launch_bounds__(THREADS, 2)
 whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ items,
              const u32 *__restrict__ tile_item, const u64 *__restrict__ cell_off, u64 *__restrict__ status,
-             u64 *__restrict__ orand, u64 *__restrict__ dlight, Counters *__restrict__ ctrs, u32 tile_h, u32 rw,
-             u32 key_words, const Model *__restrict__ model, const u32 *__restrict__ epoch, u64 wait_ns,
-             u32 inject_chunk)
+             u64 *__restrict__ orand, Counters *__restrict__ ctrs, u32 tile_h, u32 rw, u32 key_words,
+             const Model *__restrict__ model, const u32 *__restrict__ epoch, u64 wait_ns, u32 inject_chunk)
 {
     constexpr int NW = THREADS / 32;
     __shared__ u32 cnt[KMAX];
-    __shared__ u32 light[RADIX];         // records per value whose key is not heavy (model low digit only)
+    __shared__ u64 bmin[KMAX], bmax[KMAX];  // learned pass: key range of every bucket in the chunk
     __shared__ u64 red_or[NW], red_and[NW];
     __shared__ u32 s_tile, s_err;
-    extern __shared__ u64 heavy[];       // the model's heavy keys (dynamic: HEAVY_MAX words with a model)
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     if (tid == 0)
         s_err = ld_relaxed_u32(&ctrs->err);
@@ -145,9 +142,6 @@ whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const Work
         return;  // an earlier step failed (its lists may be incomplete)
     const u32 n_tiles = ctrs->grid_cur_tiles;
     const u32 ep = *epoch & LB_EPOCH_MASK;
-    const u32 n_heavy = model ? model->n_heavy : 0u;
-    for (u32 i = tid; i < n_heavy; i += THREADS)
-        heavy[i] = model->heavy[i];
     for (;;) {
         if (tid == 0)
             s_tile = atomicAdd(&ctrs->tile_ctr[0], 1u);
@@ -162,10 +156,13 @@ whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const Work
         const u32 j = t - item.tile_base;
         const u64 lo = item.begin + (u64)j * tile_h;
         const u64 hi = min(item.begin + item.count, lo + tile_h);
-        for (u32 d = tid; d < K; d += THREADS)
+        for (u32 d = tid; d < K; d += THREADS) {
             cnt[d] = 0;
-        if (tid < RADIX)
-            light[tid] = 0;
+            if (g.learned) {
+                bmin[d] = ~0ull;
+                bmax[d] = 0;
+            }
+        }
         __syncthreads();
         const u64 *src = (item.flags & ITEM_IN_TMP) ? tmp : in;
         const bool two = g.learned == 0 && g.win.wh != g.win.wl;
@@ -186,8 +183,10 @@ whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const Work
                 if (valid) {
                     vor |= kl[u];
                     vand &= kl[u];
-                    if (g.learned == 2 && !is_heavy(heavy, n_heavy, kl[u]))
-                        atomicAdd(&light[d], 1u);
+                    if (g.learned) {
+                        atomicMin(&bmin[d], kl[u]);
+                        atomicMax(&bmax[d], kl[u]);
+                    }
                 }
                 // one add for a warp whose lanes share a value (skewed data), else one per lane
                 const u32 d0 = __shfl_sync(FULL_MASK, d, 0);
@@ -235,8 +234,12 @@ whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const Work
             atomicAnd(&orand[2ull * slot + 1], a2);
             atomicAdd(&ctrs->hist_bytes, (hi - lo) * (u64)min(rw * 8u, two ? 32u : 32u));
         }
-        if (g.learned == 2 && tid < RADIX && light[tid])
-            atomicAdd(&dlight[(u64)slot * RADIX + tid], (u64)light[tid]);
+        if (g.learned)
+            for (u32 d = tid; d < K; d += THREADS)
+                if (cnt[d]) {
+                    atomicMin(&model->bmin[d], bmin[d]);
+                    atomicMax(&model->bmax[d], bmax[d]);
+                }
         __syncthreads();
     }
 }
@@ -640,25 +643,23 @@ u32 wscatter_grid(const Shape &s)
 }
 
 cudaError_t launch_whist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items, const u32 *tile_item,
-                         const u64 *cell_off, u64 *status, u64 *orand, u64 *dlight, Counters *ctrs, const Model *model,
+                         const u64 *cell_off, u64 *status, u64 *orand, Counters *ctrs, const Model *model,
                          const u32 *epoch, u64 wait_ns, u32 inject_chunk, cudaStream_t st)
 {
-    const size_t dyn = model ? (size_t)HEAVY_MAX * 8 : 0;
-    if (model) {
-        const cudaError_t e = cudaFuncSetAttribute(whist_kernel<WHIST_THREADS, WHIST_UNROLL>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess)
-            return e;
+    static thread_local int cached_dev = -1;
+    static thread_local u32 grid = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whist_kernel<WHIST_THREADS, WHIST_UNROLL>,
+                                                      WHIST_THREADS, 0);
+        grid = sm_count() * (u32)(per_sm < 1 ? 1 : per_sm);
+        cached_dev = dev;
     }
-    // resident CTAs per SM for the shared memory this launch uses (the heavy-key
-    // list only with a model)
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whist_kernel<WHIST_THREADS, WHIST_UNROLL>, WHIST_THREADS,
-                                                  dyn);
-    const u32 grid = sm_count() * (u32)(per_sm < 1 ? 1 : per_sm);
-    whist_kernel<WHIST_THREADS, WHIST_UNROLL><<<grid, WHIST_THREADS, dyn, st>>>(
-        in, tmp, items, tile_item, cell_off, status, orand, dlight, ctrs, s.tile_h, s.rw, s.key_words, model, epoch,
-        wait_ns, inject_chunk);
+    whist_kernel<WHIST_THREADS, WHIST_UNROLL><<<grid, WHIST_THREADS, 0, st>>>(
+        in, tmp, items, tile_item, cell_off, status, orand, ctrs, s.tile_h, s.rw, s.key_words, model, epoch, wait_ns,
+        inject_chunk);
     return cudaGetLastError();
 }
 

@@ -166,6 +166,64 @@ def test_warm_start_is_the_sample_cdf_at_the_knots():
     m.close()
 
 
+@pytest.mark.parametrize("name,kb", [("skewed16", 8), ("widekey32", 16)])
+def test_balance_ratio_matches_reference(name, kb):
+    """The learned partition's balance check against a reference computed apart
+    from it: the same model (warm start only, so the fit is deterministic) and
+    its key sample; the heavy keys are the sample's runs of at least S / B
+    equal keys; the buckets of the other sample keys come from
+    raduls_model_buckets (pinned to the reference map above); the ratio is the
+    largest bucket load over S / B."""
+    import torch
+    p = lib()
+    n = 1 << 21
+    recs = datagen.WORKLOADS[name](n)
+    rw = recs.shape[1]
+    d = to_dev(recs)
+    m = p.RaduLSModel(d, n, rw * 8, kb, log2_buckets=10, train_steps=0x80000000)
+    sample = m.copy_out()["sample"]
+    S = sample.size
+    thr = max(2, S >> 10)
+    starts = np.concatenate([[0], np.flatnonzero(sample[1:] != sample[:-1]) + 1])
+    runs = np.diff(np.concatenate([starts, [S]]))
+    heavy = sample[starts[runs >= thr]]
+    light = sample[~np.isin(sample, heavy)]
+    keys = torch.from_numpy(light.view(np.int64).copy()).cuda()
+    b = torch.zeros(light.size, dtype=torch.int32, device="cuda")
+    m.buckets(keys, b)
+    load = np.bincount(b.cpu().numpy().astype(np.int64), minlength=1024)
+    ratio_ref = np.float32(load.max() / (S / 1024))
+    t = scratch(n, rw)
+    d2 = to_dev(recs)
+    st = p.raduls_sort_ex(d2, t, n, rw * 8, kb, mode="learned", learned_log2_buckets=10, train_steps=0x80000000,
+                          fallback_ratio=1e9, stats=True)
+    assert p.raduls_stream_status() == 0
+    assert st["learned_used"] == 1 and st["learned_fell_back"] == 0
+    print(f"{name}: ratio {st['learned_ratio']:.3f} (reference {ratio_ref:.3f}), {heavy.size} heavy keys")
+    assert np.float32(st["learned_ratio"]) == ratio_ref
+    m.close()
+
+
+def test_one_key_buckets_need_no_more_passes(oracle_mod):
+    """Buckets holding a single key value are finished by the learned pass:
+    with 20 distinct keys in 2^21 records, nothing is left for another
+    distribution pass after it, and the output is the oracle's."""
+    p = lib()
+    n = 1 << 21
+    rng = np.random.default_rng(9)
+    vals = np.sort(rng.integers(0, 1 << 63, size=20, dtype=np.uint64))
+    recs = np.empty((n, 2), dtype=np.uint64)
+    recs[:, 0] = vals[rng.integers(0, 20, n)]
+    recs[:, 1] = np.arange(n, dtype=np.uint64)
+    d = to_dev(recs)
+    t = scratch(n, 2)
+    st = p.raduls_sort_ex(d, t, n, 16, 8, mode="learned", fallback_ratio=1e9, stats=True)
+    assert p.raduls_stream_status() == 0
+    assert st["learned_used"] == 1
+    assert st["grid_passes"] == 1 and st["block_items"] == 0 and st["bucket_items"] == 0
+    np.testing.assert_array_equal(from_dev(d, n, 2), oracle_mod.sort(recs, 8, threads=8))
+
+
 @pytest.mark.parametrize("name,n", [("skewed16", 1 << 22), ("widekey32", 1 << 21), ("uniform16", 1 << 21)])
 def test_learned_sort_matches_oracle(oracle_mod, name, n):
     recs = datagen.WORKLOADS[name](n)
