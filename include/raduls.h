@@ -102,7 +102,7 @@ typedef struct {
     uint32_t mode;                  /* 0 AUTO (currently the plain passes: the learned first
                                        partition is not yet faster on skewed keys), 1 PLAIN,
                                        2 LEARNED */
-    uint32_t learned_log2_buckets;  /* buckets of the learned pass, log2: 8..10, 0 = 10 */
+    uint32_t learned_log2_buckets;  /* buckets of the learned pass, log2: 8..10, 0 = 8 */
     float    fallback_ratio;        /* learned partition is rejected above this max/ideal ratio
                                        (over buckets whose key word 0 varies); 0 = 4.0 */
     uint32_t train_steps;           /* Adam steps per stage of the model fit: 0 = 16, at most

@@ -17,7 +17,7 @@ namespace raduls {
 // ------------------------------------------------------------------ kernel
 
 template <int THREADS, int K, int RW>
-__global__ void __launch_bounds__(THREADS, THREADS >= 512 ? 2 : 4)
+__global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : THREADS >= 512 ? 2 : 4)
 block_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ blocks,
                   Counters *__restrict__ ctrs, u32 rw_rt, u32 key_words, const u64 *__restrict__ seg_off)
 {
@@ -47,7 +47,8 @@ namespace {
     X(1, 512, 8, 2)       \
     X(2, 512, 4, 4)       \
     X(3, 512, 2, 0)       \
-    X(4, 256, 1, 0)
+    X(4, 256, 1, 0)       \
+    X(5, 1024, 8, 2)
 
 template <int THREADS, int K, int RW>
 cudaError_t prepare_block(u32 rw, size_t *smem)

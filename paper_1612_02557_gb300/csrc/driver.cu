@@ -120,6 +120,10 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
             s.scat_var = t.scat_var;
         if (t.cap_b > WARP_BIN && t.cap_b <= s.cap_b)
             s.cap_b = t.cap_b;
+        else if (rw == 2 && t.cap_b == block_cap_of(5)) {
+            s.block_var = 5;  // the on-chip class of twice the size (one CTA of 1024 threads per SM)
+            s.cap_b = t.cap_b;
+        }
         if (s.bucket_var >= 0)
             s.bucket_max = t.bucket_max;
         if (t.wmax >= 8 && t.wmax <= WIDE_MAX)
@@ -133,6 +137,15 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     }
     if (const char *v = getenv("RADULS_LEAF"))
         s.leaf = (u32)strtoul(v, nullptr, 10);
+    if (const char *v = getenv("RADULS_BLOCK_CAP")) {
+        const u32 want = (u32)strtoul(v, nullptr, 10);
+        if (rw == 2 && want == block_cap_of(5)) {
+            s.block_var = 5;
+            s.cap_b = want;
+        } else if (want > WARP_BIN && want <= block_cap_of(s.block_var)) {
+            s.cap_b = want;
+        }
+    }
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
         if (scatter_variant_fits(want, rw))
@@ -641,8 +654,10 @@ int model_fit(Ctx &c, ModelBufs &M, const u64 *in, u64 n, u32 rw, const u64 *roo
     return RADULS_OK;
 }
 
-// Buckets of the learned pass: as many as one distribution pass splits into.
-u32 default_log2b() { return WIDE_MAX; }
+// Buckets of the learned pass: 256 (measured on the skewed and wide-key
+// workloads: 120 ms against 132 ms with 1,024 at 2^30 x 16 B, since the pass
+// then runs with the two-CTA distribution shape).
+u32 default_log2b() { return 8u; }
 
 // ---------------------------------------------------------------- the sort
 
@@ -1648,6 +1663,15 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
             continue;
         Tuned t = best;
         t.leaf = leaves[li];
+        time_one(t, ms);
+    }
+    if (rc == RADULS_OK && rw == 2) {
+        // the on-chip class at twice the size
+        Tuned t = best;
+        t.cap_b = block_cap_of(5);
+        if (t.bucket_max && t.bucket_max <= t.cap_b)
+            t.bucket_max = 0;
+        t.leaf = 0;
         time_one(t, ms);
     }
     if (rc == RADULS_OK && base.cap_b / 2u > WARP_BIN) {

@@ -63,10 +63,10 @@ __device__ __forceinline__ bool bucket_single_key(const PlanArgs &a, u32 c)
     return a.model && a.model->bmin[c] == a.model->bmax[c];
 }
 
-// A learned bucket of more than cap_b records: its key bytes share nothing
-// known, so it is sorted from the top of the key (its constant bits are
-// skipped by the next pass's histogram), or from key word 1 when its word 0
-// is one value; a one-word bucket of one value is finished.
+// A learned bucket of more than cap_b records: sorted from the highest bit of
+// key word 0 that varies inside it (from its smallest and largest key), or
+// from key word 1 when its word 0 is one value; a one-word bucket of one
+// value is finished.
 __device__ __forceinline__ void learned_child(const PlanArgs &a, u32 c, u64 begin, u64 count, u32 flags)
 {
     if (bucket_single_key(a, c)) {
@@ -76,7 +76,10 @@ __device__ __forceinline__ void learned_child(const PlanArgs &a, u32 c, u64 begi
             append_copy(a, begin, count);
         return;
     }
-    append_bin(a, begin, count, a.top_digit, flags);
+    // the bucket's keys agree on every bit of word 0 above the highest one in
+    // which its smallest and largest key differ: the next pass starts there
+    const u64 diff = a.model->bmin[c] ^ a.model->bmax[c];
+    append_bin_hi(a, begin, count, 64u * (a.key_words - 1u) + 64u - (u32)__clzll((long long)diff), flags);
 }
 
 // The highest key bit below `lo` that may still vary inside a bin whose key
