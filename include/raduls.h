@@ -285,8 +285,9 @@ typedef struct {
     uint32_t bucket_max;       /* largest mid-size bin sorted by one CTA through L2 (0: class off) */
     float    best_ms;          /* sort time of the chosen setting on the tuning input */
     uint32_t candidates;       /* settings timed */
-    uint32_t digit_bits;       /* widest digit of a distribution pass, in bits (8..12) */
+    uint32_t digit_bits;       /* widest digit of a distribution pass, in bits (8..10) */
     uint32_t leaf;             /* sub-bin size (records) the digit widths aim at */
+    uint32_t bin_sort;         /* 1: small bins go to the streamed on-chip sort first */
 } raduls_tuning;
 
 /* Autotuner of the launch shapes and size-class thresholds (the paper has no

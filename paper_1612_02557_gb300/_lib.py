@@ -271,6 +271,7 @@ class Tuning(ctypes.Structure):
         ("candidates", ctypes.c_uint32),
         ("digit_bits", ctypes.c_uint32),
         ("leaf", ctypes.c_uint32),
+        ("bin_sort", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:

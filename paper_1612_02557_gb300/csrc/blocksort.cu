@@ -19,16 +19,18 @@ namespace raduls {
 template <int THREADS, int K, int RW>
 __global__ void __launch_bounds__(THREADS, THREADS >= 1024 ? 1 : THREADS >= 512 ? 2 : 4)
 block_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ blocks,
-                  Counters *__restrict__ ctrs, u32 rw_rt, u32 key_words, const u64 *__restrict__ seg_off)
+                  Counters *__restrict__ ctrs, u32 rw_rt, u32 key_words, const u64 *__restrict__ seg_off, u32 fb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<THREADS, K> &sm = *reinterpret_cast<BlockSmem<THREADS, K> *>(smem_raw);
     if (cta_failed(ctrs))
         return;
-    const u64 n_items = ctrs->block;
+    // the on-chip list, or the items the streamed bin sort left to this kernel
+    const u64 n_items = fb ? ctrs->block_fb : ctrs->block;
+    u32 *const ctr = fb ? &ctrs->fb_ctr : &ctrs->tile_ctr[3];
     for (;;) {
         if (threadIdx.x == 0)
-            sm.item = atomicAdd(&ctrs->tile_ctr[3], 1u);
+            sm.item = atomicAdd(ctr, 1u);
         __syncthreads();
         const u64 ii = sm.item;
         if (ii >= n_items)
@@ -92,7 +94,7 @@ u32 block_grid(const Shape &s)
 }
 
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks, Counters *ctrs,
-                              const u64 *seg_off, cudaStream_t st)
+                              const u64 *seg_off, cudaStream_t st, bool fb)
 {
     const u32 grid = block_grid(s);
     switch (s.block_var) {
@@ -103,7 +105,7 @@ cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const Wor
         if (e != cudaSuccess)                                                                       \
             return e;                                                                               \
         block_sort_kernel<T, K, RW><<<grid, T, smem, st>>>(in, tmp, blocks, ctrs, s.rw, s.key_words,  \
-                                                           seg_off);                              \
+                                                           seg_off, fb ? 1u : 0u);                \
         return cudaGetLastError();                                                                  \
     }
         BLOCK_VARIANTS(X)

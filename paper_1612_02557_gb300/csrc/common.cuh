@@ -170,6 +170,11 @@ struct Counters {
     u32 learned_ok;       // 1 while the learned partition passes its balance check
     float learned_ratio;  // max bucket / ideal bucket of the learned partition (0 = not measured)
     u32 learned_fell_back;
+    u64 block_fb;         // on-chip items the streamed bin sort left to the general on-chip kernel
+    u32 fb_ctr;           // dynamic item counter of the general on-chip kernel over those items
+    u32 wmax_cur;         // widest digit (bits) of the current grid list's items
+    u32 wmax_next;        // widest digit of the items appended to the next grid list
+    u32 pad_fb;
 };
 
 // Capacities of the device lists (set by the host from n and the tile sizes).
@@ -451,6 +456,56 @@ __device__ __forceinline__ void discard_l2_line(const void *p)
 __device__ __forceinline__ void set_error(Counters *c, u32 code)
 {
     atomicCAS(&c->err, 0u, code);
+}
+
+// Largest single bulk copy of tile_load (bytes, a multiple of 16).
+#ifndef RADULS_TILE_PIECE
+#define RADULS_TILE_PIECE 262144
+#endif
+constexpr u32 TILE_PIECE = RADULS_TILE_PIECE;
+
+// Start loading records [a, b) of `src` (rw words each) into buffer `buf`:
+// the 16-byte-aligned body with one bulk asynchronous copy completing on
+// `bar`, at most one leading and one trailing word directly.  The buffer keeps
+// the global 16-byte phase (returned: the word offset of record a).  Called
+// by one thread; the direct words are visible after the next barrier.
+__device__ __forceinline__ u32 tile_load(u64 *buf, const u64 *src, u64 a, u64 b, u32 rw, u64 *bar)
+{
+    const u64 w0 = a * rw, w1 = b * rw;
+    const u32 ph = (u32)(w0 & 1u);
+    u64 *dst = buf + ph;                    // dst[i] holds global word w0 + i
+    u64 body0 = w0 + ph, body1 = w1 & ~1ull;  // even word bounds: 16-byte aligned
+    if (ph && w0 < w1)
+        dst[0] = __ldcg(src + w0);
+    if ((w1 & 1u) && w1 - 1 >= w0 + ph)
+        dst[w1 - 1 - w0] = __ldcg(src + w1 - 1);
+    const u32 bytes = body1 > body0 ? (u32)((body1 - body0) * 8u) : 0u;
+    mbar_arrive_expect_tx(bar, bytes);
+    // in pieces of at most TILE_PIECE bytes, all completing on the one barrier
+    for (u32 off = 0; off < bytes; off += TILE_PIECE) {
+        const u32 len = bytes - off < TILE_PIECE ? bytes - off : TILE_PIECE;
+        bulk_copy_g2s(reinterpret_cast<char *>(dst + (body0 - w0)) + off,
+                      reinterpret_cast<const char *>(src + body0) + off, len, bar);
+    }
+    return ph;
+}
+
+// Bounded wait for a bulk copy's completion (phase parity `par`), by the one
+// thread that issues the copies; the barrier after it hands the tile to the
+// rest of the CTA.  False on timeout (the error is recorded).
+__device__ __forceinline__ bool tile_wait(u64 *bar, u32 par, Counters *ctrs, u64 wait_ns)
+{
+    if (mbar_try_wait(bar, par))
+        return true;
+    const u64 t0 = global_timer_ns();
+    for (u32 spins = 0;; ++spins) {
+        if (mbar_try_wait(bar, par))
+            return true;
+        if ((spins & 63u) == 63u && global_timer_ns() - t0 > wait_ns) {
+            set_error(ctrs, ST_TIMEOUT);
+            return false;
+        }
+    }
 }
 
 // True in every thread of the CTA when an earlier step recorded an error (its

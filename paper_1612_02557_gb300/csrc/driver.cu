@@ -36,6 +36,8 @@ bool scatter_variant_fits(int v, u32 rw)
     case 1:
     case 5:
     case 8:
+    case 9:
+    case 10:
         return rw == 2;
     case 6:
         return rw == 1;
@@ -62,6 +64,7 @@ struct Tuned {
     u32 bucket_max = 0;
     u32 wmax = 0;   // widest digit of a distribution pass (0: default)
     u32 leaf = 0;   // sub-bin size the digit widths aim at (0: default)
+    int bins = 0;   // streamed on-chip finisher: 0 default, 1 on, 2 off
 };
 constexpr int TUNE_DEVICES = 64;
 Tuned g_tuned[TUNE_DEVICES][2][33];
@@ -83,7 +86,9 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
         s.scat_var = 6;
         s.block_var = 0;
     } else if (rw == 2) {
-        s.scat_var = 5;
+        // plain sorts: digits of up to 10 bits, two CTAs per SM; batched sorts
+        // keep 8-bit digits (their arrays are mostly below one chunk)
+        s.scat_var = batched ? 5 : 10;
         s.block_var = 1;
     } else if (rw == 4) {
         s.scat_var = 7;
@@ -120,8 +125,11 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
             s.scat_var = t.scat_var;
         if (t.cap_b > WARP_BIN && t.cap_b <= s.cap_b)
             s.cap_b = t.cap_b;
-        else if (rw == 2 && t.cap_b == block_cap_of(5)) {
-            s.block_var = 5;  // the on-chip class of twice the size (one CTA of 1024 threads per SM)
+        else if (rw == 2 && !batched && t.cap_b == block_cap_of(5)) {
+            // the on-chip class of twice the size (one CTA of 1024 threads per
+            // SM); batched sorts keep theirs: the persistent kernel's on-chip
+            // items hold at most 4,096 records
+            s.block_var = 5;
             s.cap_b = t.cap_b;
         }
         if (s.bucket_var >= 0)
@@ -139,30 +147,65 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
         s.leaf = (u32)strtoul(v, nullptr, 10);
     if (const char *v = getenv("RADULS_BLOCK_CAP")) {
         const u32 want = (u32)strtoul(v, nullptr, 10);
-        if (rw == 2 && want == block_cap_of(5)) {
+        if (rw == 2 && !batched && want == block_cap_of(5)) {
             s.block_var = 5;
             s.cap_b = want;
         } else if (want > WARP_BIN && want <= block_cap_of(s.block_var)) {
             s.cap_b = want;
         }
     }
+    // plain sorts of 16-byte records: each level takes the two-CTA shape made
+    // for its widest digit (variant 5: 8 bits, 9: 9 bits, 10: 10 bits)
+    s.scat_by_width = rw == 2 && !batched && (s.scat_var == 9 || s.scat_var == 10);
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
-        if (scatter_variant_fits(want, rw))
+        if (scatter_variant_fits(want, rw)) {
             s.scat_var = want;
+            s.scat_by_width = false;  // one shape for every level
+        }
     }
     if (const char *v = getenv("RADULS_BUCKET_MAX"))
         s.bucket_max = s.bucket_var < 0 ? 0u : (u32)strtoul(v, nullptr, 10);
+    // the streamed on-chip finisher (plain sorts): its capacity becomes the
+    // on-chip class, and the general on-chip kernel (of at least that
+    // capacity) takes what it leaves
+    s.bins_var = -1;
+    {
+        int want = (t.valid && t.bins) ? t.bins : 1;  // on unless tuned off
+        if (const char *v = getenv("RADULS_BIN_SORT"))
+            want = atoi(v) ? 1 : 2;
+        int bv = batched ? -1 : binsort_variant_for(rw);
+        if (const char *v = getenv("RADULS_BIN_VARIANT"))
+            if (bv >= 0 && binsort_rw_of(atoi(v)) == rw)
+                bv = atoi(v);
+        if (want == 1 && bv >= 0 && rw == 2) {
+            s.bins_var = bv;
+            s.block_var = 5;
+            const u32 bcap = binsort_cap_of(bv);
+            s.cap_b = (t.valid && t.cap_b > WARP_BIN && t.cap_b < bcap) ? t.cap_b : bcap;
+            if (s.leaf == 0)
+                s.leaf = s.cap_b / 5u * 4u;  // bins of about 4/5 of the capacity: the largest still fit
+        }
+    }
     s.tile_s = wscatter_tile_of(s.scat_var);
     while (s.wmax > 8u && (1u << s.wmax) > wscatter_kmax_of(s.scat_var))
         --s.wmax;  // the variant handles no wider digit
-    if (s.leaf == 0 || s.leaf > s.cap_b)
-        s.leaf = s.cap_b / 4u * 3u;  // sub-bins of about 3/4 of the on-chip class: the largest still fit
     if (s.bucket_max > BUCKET_IDX_MAX)  // positions inside a mid-size bin are 16-bit
         s.bucket_max = BUCKET_IDX_MAX;
     if (s.bucket_max <= s.cap_b)
         s.bucket_max = 0;
+    // the sub-bin size the digit widths aim at: at most the largest bin a
+    // finisher takes (the mid-size class where there is one)
+    if (s.leaf == 0 || s.leaf > (s.bucket_max > s.cap_b ? s.bucket_max : s.cap_b))
+        s.leaf = s.cap_b / 4u * 3u;  // sub-bins of about 3/4 of the on-chip class: the largest still fit
     return s;
+}
+
+int level_scatter_variant(const Shape &s, u32 w)
+{
+    if (!s.scat_by_width)
+        return s.scat_var;
+    return w <= 8u ? 5 : w == 9u ? 9 : 10;
 }
 
 namespace {
@@ -268,6 +311,7 @@ struct Lists {
     WorkItem *bkt[2];
     WorkItem *bkt_split;
     WorkItem *blocks;
+    WorkItem *blocks_fb;  // on-chip items the streamed bin sort leaves to the general kernel
     WorkItem *copies;
     u32 *tile_hist;
     u32 *tile_copy;
@@ -368,7 +412,8 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
         block_cap = n + 4;
     if (grid_cap > 0xffffffffull || hist_tiles > 0xffffffffull || copy_tiles > 0xffffffffull)
         return cudaErrorInvalidValue;
-    size_t off = 0, o_grid0, o_grid1, o_scat, o_bkt0, o_bkt1, o_bkts, o_blocks, o_copies, o_th, o_tc, o_c0, o_c1;
+    size_t off = 0, o_grid0, o_grid1, o_scat, o_bkt0, o_bkt1, o_bkts, o_blocks, o_fb, o_copies, o_th, o_tc, o_c0,
+           o_c1;
     o_grid0 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_grid1 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_scat = off; off = align256(off + grid_cap * sizeof(WorkItem));
@@ -376,6 +421,7 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
     o_bkt1 = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_bkts = off; off = align256(off + grid_cap * sizeof(WorkItem));
     o_blocks = off; off = align256(off + block_cap * sizeof(WorkItem));
+    o_fb = off; off = align256(off + (s.bins_var >= 0 ? block_cap : 1) * sizeof(WorkItem));
     o_copies = off; off = align256(off + copy_cap * sizeof(WorkItem));
     o_th = off; off = align256(off + hist_tiles * 4);
     o_tc = off; off = align256(off + copy_tiles * 4);
@@ -392,6 +438,7 @@ cudaError_t work_lists(Work &wk, const Shape &s, u64 n, Lists &L)
     L.bkt[1] = (WorkItem *)(b + o_bkt1);
     L.bkt_split = (WorkItem *)(b + o_bkts);
     L.blocks = (WorkItem *)(b + o_blocks);
+    L.blocks_fb = (WorkItem *)(b + o_fb);
     L.copies = (WorkItem *)(b + o_copies);
     L.tile_hist = (u32 *)(b + o_th);
     L.tile_copy = (u32 *)(b + o_tc);
@@ -701,6 +748,8 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
     const bool whole_mid = !step_api && j.n > s.cap_b && j.n <= bmax;
     u32 n_grid = (step_api || (j.n > s.cap_b && !whole_mid)) ? 1u : 0u;
     u32 n_bkt = whole_mid ? 1u : 0u;
+    // the widest digit of the current level (the first: init_kernel's choice)
+    u32 lvl_w = (init_wmax > 0 && !step_api) ? pick_width(j.n, 8u * top + 8u, s.leaf, init_wmax) : 8u;
     for (u32 level = 0; n_grid > 0 || n_bkt > 0; ++level) {
         PlanArgs a{};
         a.grid_cur = L.grid[cur];
@@ -792,9 +841,11 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             a.tile_scat = B.tile_scat;
             a.model = model;
             TIMED(RADULS_K_PLAN, launch_plan(a, n_grid, st));
-            // the learned pass needs a distribution shape that takes 2^log2b values
+            // the level's shape for its widest digit; the learned pass needs
+            // one that takes 2^log2b values
             Shape sl = s;
-            if (model && ((u64)1 << log2b) > wscatter_kmax_of(s.scat_var))
+            sl.scat_var = level_scatter_variant(s, model ? log2b : lvl_w);
+            if (model && ((u64)1 << log2b) > wscatter_kmax_of(sl.scat_var))
                 sl.scat_var = wide_scatter_variant(j.rw);
             TIMED(RADULS_K_SCATTER, launch_wscatter(sl, j.in, j.tmp, L.scat, B.tile_scat, L.cell[cur], B.status,
                                                     wk.ctrs, model, c.wait_ns, st));
@@ -834,13 +885,20 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             break;
         n_grid = wk.h_ctrs->grid_cur;
         n_bkt = wk.h_ctrs->bucket_cur;
+        lvl_w = wk.h_ctrs->wmax_cur ? wk.h_ctrs->wmax_cur : 8u;
         cur ^= 1;
     }
     if (j.hout && (wk.h_ctrs->block || wk.h_ctrs->copy || wk.h_ctrs->err))
         j.hout->copied = false;  // records still move after the last level
     if (!step_api) {
         TIMED(RADULS_K_COPY, launch_copy(s, j.in, j.tmp, L.copies, L.tile_copy, wk.ctrs, st));
-        TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks, wk.ctrs, nullptr, st));
+        if (s.bins_var >= 0) {
+            TIMED(RADULS_K_BLOCK, launch_bin_sort(s.bins_var, j.in, j.tmp, L.blocks, L.blocks_fb, wk.ctrs,
+                                                  s.key_words, L.caps.block, c.wait_ns, st));
+            TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks_fb, wk.ctrs, nullptr, st, true));
+        } else {
+            TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks, wk.ctrs, nullptr, st));
+        }
     }
     CK(rec.begin(RADULS_K_SETUP));
     fold_status_kernel<<<1, 1, 0, st>>>(wk.ctrs, c.dev_status);
@@ -1641,7 +1699,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     }
     time_one(best, ms);
     const Tuned base_t = best;
-    for (int v = 0; v < 9 && rc == RADULS_OK; ++v) {
+    for (int v = 0; v < 11 && rc == RADULS_OK; ++v) {
         if (v == base.scat_var || !scatter_variant_fits(v, rw) || ((v == 3 || v == 4) && rw <= 4))
             continue;
         Tuned t = best;
@@ -1665,7 +1723,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
         t.leaf = leaves[li];
         time_one(t, ms);
     }
-    if (rc == RADULS_OK && rw == 2) {
+    if (rc == RADULS_OK && rw == 2 && !batched && base.bins_var < 0) {
         // the on-chip class at twice the size
         Tuned t = best;
         t.cap_b = block_cap_of(5);
@@ -1683,6 +1741,14 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
             t.bucket_max = 0;
         time_one(t, ms);
     }
+    if (rc == RADULS_OK && base.bins_var >= 0) {
+        // the general on-chip kernel alone (the streamed bin sort off)
+        Tuned t = best;
+        t.bins = 2;
+        t.cap_b = 0;
+        t.leaf = 0;
+        time_one(t, ms);
+    }
     const u32 bmaxes[2] = {base.bucket_max / 2u, 0u};
     for (int bi = 0; bi < 2 && base.bucket_max && rc == RADULS_OK; ++bi) {
         Tuned t = best;
@@ -1695,7 +1761,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     // each: the default stays unless the winner is clearly faster
     if (rc == RADULS_OK && (best.scat_var != base_t.scat_var || best.wmax != base_t.wmax ||
                             best.leaf != base_t.leaf || best.cap_b != base_t.cap_b ||
-                            best.bucket_max != base_t.bucket_max)) {
+                            best.bucket_max != base_t.bucket_max || best.bins != base_t.bins)) {
         const Tuned win = best;
         float mw = 1e30f, mb = 1e30f;
         for (int i = 0; i < 3 && rc == RADULS_OK; ++i) {
@@ -1733,6 +1799,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
         out->candidates = timed;
         out->digit_bits = best.wmax;
         out->leaf = best.leaf;
+        out->bin_sort = best.bins == 2 ? 0u : (base.bins_var >= 0 ? 1u : 0u);
     }
     return RADULS_OK;
 }

@@ -19,7 +19,12 @@ struct Shape {
     int bucket_var;  // mid-size bin kernel variant (-1: none for this record width)
     u32 leaf;        // sub-bin size the distribution passes' digit widths aim at
     u32 wmax;        // widest digit of a distribution pass (bits, 8..WIDE_MAX)
+    int bins_var;    // streamed on-chip finisher variant (-1: the general on-chip kernel alone)
+    bool scat_by_width;  // each level's distribution shape follows its widest digit
 };
+
+// The distribution shape of a level whose widest digit has w bits.
+int level_scatter_variant(const Shape &s, u32 w);
 
 Shape choose_shape(u32 rw, u32 key_words, bool batched = false);
 
@@ -32,8 +37,20 @@ u32 copy_grid();
 // entry points): per-bin rows of 256 counts and the OR / AND of the key word.
 cudaError_t launch_hist(const Shape &s, const u64 *in, const u64 *tmp, const WorkItem *items,
                         const u32 *tile_item, u64 *hist, u64 *orand, Counters *ctrs, cudaStream_t st);
+// fb: the list of items the streamed bin sort left (count block_fb) instead
+// of the on-chip list itself (count block).
 cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const WorkItem *blocks,
-                              Counters *ctrs, const u64 *seg_off, cudaStream_t st);
+                              Counters *ctrs, const u64 *seg_off, cudaStream_t st, bool fb = false);
+
+// The streamed on-chip finisher (binsort.cu): every on-chip item it can take
+// (a single bin or a run of one parent's sub-bins, up to its capacity) sorted
+// in shared memory while the next one loads; the rest go to `fb` (capacity
+// fb_cap) for launch_block_sort(..., fb = true).  -1 / 0: no variant for rw.
+int binsort_variant_for(u32 rw);
+u32 binsort_cap_of(int var);
+u32 binsort_rw_of(int var);
+cudaError_t launch_bin_sort(int var, u64 *in, const u64 *tmp, const WorkItem *blocks, WorkItem *fb, Counters *ctrs,
+                            u32 key_words, u64 fb_cap, u64 wait_ns, cudaStream_t st);
 
 // The distribution pass over chunks (wide.cu): a histogram of every chunk's
 // digit window whose counts are chained along each bin's chunks by a
@@ -107,6 +124,7 @@ __device__ __forceinline__ void append_grid_item(const PlanArgs &a, u64 begin, u
                                                  u32 w)
 {
     const u32 slot = atomicAdd(&a.ctrs->grid_next, 1u);
+    atomicMax(&a.ctrs->wmax_next, w);
     const u32 nt = ceil_div_u64(count, a.tile_h);
     const u32 tb = atomicAdd(&a.ctrs->grid_next_tiles, nt);
     const u64 cells = (u64)nt << w;
@@ -132,7 +150,8 @@ __device__ __forceinline__ void append_grid_item(const PlanArgs &a, u64 begin, u
 // mid-size bin goes to the next level's mid-size list (no histogram pass: its
 // kernel counts for itself, from the byte holding bit hi - 1 down), any other
 // to the next grid list with a digit width picked for its size.
-__device__ __forceinline__ void append_bin_hi(const PlanArgs &a, u64 begin, u64 count, u32 hi, u32 flags)
+__device__ __forceinline__ void append_bin_hi(const PlanArgs &a, u64 begin, u64 count, u32 hi, u32 flags,
+                                              u32 wmax = 0)
 {
     flags &= ~(ITEM_W_MASK | ITEM_C_MASK);
     if (a.bucket_max && count <= a.bucket_max) {
@@ -151,7 +170,7 @@ __device__ __forceinline__ void append_bin_hi(const PlanArgs &a, u64 begin, u64 
         a.buckets_next[slot] = it;
         return;
     }
-    const u32 w = pick_width(count, hi, a.leaf, a.wmax);
+    const u32 w = pick_width(count, hi, a.leaf, wmax ? wmax : a.wmax);
     u32 digit, fl;
     grid_pos(hi, w, flags, digit, fl);
     append_grid_item(a, begin, count, digit, fl, w);

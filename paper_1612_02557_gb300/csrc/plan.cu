@@ -98,6 +98,7 @@ __device__ __forceinline__ u32 next_varying_hi(u32 lo, u64 vor, u64 vand)
 }
 
 constexpr u32 PLAN_THREADS = 256;
+constexpr u64 PLAN_SKEW = 8;  // a sub-bin this many times the mean marks a skewed bin
 
 // Block-wide exclusive scan of one u64 per thread (PLAN_THREADS threads);
 // `total` gets the sum.  Contains barriers.
@@ -168,13 +169,18 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
         const u32 v0 = K >= PLAN_THREADS ? tid * per : tid;
         const u32 nv = (K >= PLAN_THREADS || tid < K) ? per : 0u;
         u64 part = 0;
-        bool cst = false;
+        bool cst = false, heavy = false;
         for (u32 i = 0; i < nv; ++i) {
             const u64 h = row[v0 + i] & LB_VAL_MASK;
             part += h;
             cst |= (h == it.count);
+            heavy |= h * K > PLAN_SKEW * it.count;
         }
         const int is_const = __syncthreads_or(cst);
+        // a sub-bin far above the bin's mean: the keys are skewed, and the
+        // children split 8 bits at a time (wider digits would leave many small
+        // sub-bins behind)
+        const u32 child_wmax = __syncthreads_or(heavy) ? 8u : 0u;
         const u64 vor = a.orand[2ull * g], vand = a.orand[2ull * g + 1];
         // children skip the bits below the window that are constant in the whole bin
         const u32 chi = learned ? 0u : next_varying_hi(lo, vor, vand);
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) plan_kernel(PlanArgs a)
                 if (learned)
                     learned_child(a, c, b, h, cflags);
                 else
-                    append_bin_hi(a, b, h, chi, cflags);
+                    append_bin_hi(a, b, h, chi, cflags, child_wmax);
             }
             const bool small = !learned && h <= smallmax;
             kpart += small ? h : (1ull << 48);
@@ -416,6 +422,8 @@ __global__ void advance_kernel(Counters *c)
     c->grid_cur_tiles = c->grid_next_tiles;
     c->cells_cur = c->cells_next;
     c->cells_next = 0;
+    c->wmax_cur = c->wmax_next;
+    c->wmax_next = 0;
     c->grid_next = 0;
     c->grid_next_tiles = 0;
     c->scatter = 0;

@@ -29,6 +29,8 @@
 // A digit is a window of up to 10 key bits (the Window of common.cuh), or the
 // learned model's bucket, so one pass can split a bin 1,024 ways; the width
 // of each bin's digit is picked when the bin is planned.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace raduls {
@@ -246,14 +248,25 @@ whist_kernel(const u64 *__restrict__ in, const u64 *__restrict__ tmp, const Work
 
 // -------------------------------------------------------------- distribution
 
-template <int THREADS, int E, int KM>
+// Whether the tile's permutation keeps the element index alone (16 bits; the
+// write loop then reads the value off the record again): the one-buffer
+// shapes with digits of more than 9 bits, whose footprint would otherwise
+// keep a second CTA off the SM.
+template <int KM, int NB>
+constexpr bool wscatter_perm16()
+{
+    return KM > 512 && NB == 1;
+}
+
+template <int THREADS, int E, int KM, bool P16>
 struct WScatterSmem {
     static constexpr int NW = THREADS / 32;
+    using PermT = typename std::conditional<P16, unsigned short, u32>::type;
     unsigned short cnt[NW][KM];       // per warp: records of each value in the tile, then its offsets
     u64 cursor[KM];                   // next global position of every value in this chunk
     u64 goff[KM];                     // global position of sorted slot 0's value run, per value
     u32 tstart[KM];                   // first sorted slot of every value in the tile
-    u32 perm[THREADS * E];            // sorted slot -> element | value << 16
+    PermT perm[THREADS * E];          // sorted slot -> element (| value << 16 unless P16)
     u32 wsum[NW];
     u64 bar[2];                       // bulk-copy barriers of the two record buffers
     WorkItem item;
@@ -271,52 +284,10 @@ constexpr size_t wscatter_buf_words(u32 rw)
 template <int THREADS, int E, int KM, int NB>
 constexpr size_t wscatter_smem_bytes(u32 rw)
 {
-    return ((sizeof(WScatterSmem<THREADS, E, KM>) + 15) & ~(size_t)15) + NB * wscatter_buf_words<THREADS, E>(rw) * 8;
+    return ((sizeof(WScatterSmem<THREADS, E, KM, wscatter_perm16<KM, NB>()>) + 15) & ~(size_t)15) +
+           NB * wscatter_buf_words<THREADS, E>(rw) * 8;
 }
 
-namespace {
-
-// Start loading records [a, b) of `src` (rw words each) into buffer `buf`:
-// the 16-byte-aligned body with one bulk asynchronous copy completing on
-// `bar`, at most one leading and one trailing word directly.  The buffer keeps
-// the global 16-byte phase (returned: the word offset of record a).  Called
-// by one thread; the direct words are visible after the next barrier.
-__device__ __forceinline__ u32 tile_load(u64 *buf, const u64 *src, u64 a, u64 b, u32 rw, u64 *bar)
-{
-    const u64 w0 = a * rw, w1 = b * rw;
-    const u32 ph = (u32)(w0 & 1u);
-    u64 *dst = buf + ph;                    // dst[i] holds global word w0 + i
-    u64 body0 = w0 + ph, body1 = w1 & ~1ull;  // even word bounds: 16-byte aligned
-    if (ph && w0 < w1)
-        dst[0] = __ldcg(src + w0);
-    if ((w1 & 1u) && w1 - 1 >= w0 + ph)
-        dst[w1 - 1 - w0] = __ldcg(src + w1 - 1);
-    const u32 bytes = body1 > body0 ? (u32)((body1 - body0) * 8u) : 0u;
-    mbar_arrive_expect_tx(bar, bytes);
-    if (bytes)
-        bulk_copy_g2s(dst + (body0 - w0), src + body0, bytes, bar);
-    return ph;
-}
-
-// Bounded wait for a bulk copy's completion (phase parity `par`), by the one
-// thread that issues the copies; the barrier after it hands the tile to the
-// rest of the CTA.  False on timeout (the error is recorded).
-__device__ __forceinline__ bool tile_wait(u64 *bar, u32 par, Counters *ctrs, u64 wait_ns)
-{
-    if (mbar_try_wait(bar, par))
-        return true;
-    const u64 t0 = global_timer_ns();
-    for (u32 spins = 0;; ++spins) {
-        if (mbar_try_wait(bar, par))
-            return true;
-        if ((spins & 63u) == 63u && global_timer_ns() - t0 > wait_ns) {
-            set_error(ctrs, ST_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-}  // namespace
 
 // KM: the most digit values a launch handles (the widest digit of its level);
 // NB: record buffers -- 2, the next tile loads while this one is ranked;
@@ -334,9 +305,11 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
     static_assert(KM <= 65536 && KM <= (int)KMAX, "values are 16-bit");
     static_assert(E * 32 <= 65535, "per-warp counts are 16-bit");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WScatterSmem<THREADS, E, KM> &sm = *reinterpret_cast<WScatterSmem<THREADS, E, KM> *>(smem_raw);
+    constexpr bool P16 = wscatter_perm16<KM, NB>();
+    using Sm = WScatterSmem<THREADS, E, KM, P16>;
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
     const u32 rw = RW ? (u32)RW : rw_rt;
-    u64 *const bufs = reinterpret_cast<u64 *>(smem_raw + ((sizeof(WScatterSmem<THREADS, E, KM>) + 15) & ~(size_t)15));
+    u64 *const bufs = reinterpret_cast<u64 *>(smem_raw + ((sizeof(Sm) + 15) & ~(size_t)15));
     const size_t bw = wscatter_buf_words<THREADS, E>(rw);
     const u32 tid = threadIdx.x, lane = tid & 31u, w = tid >> 5;
     if (tid == 0) {
@@ -452,7 +425,11 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
             // warps' counts become per-warp offsets and the tile's totals an
             // exclusive prefix.  Padding elements (past m) take the largest
             // value and come last, so they shift no real element.
-            {
+            if (K >= 256u) {
+                uint4 *row = reinterpret_cast<uint4 *>(sm.cnt[w]);  // 8 counters per vector store
+                for (u32 i = lane; i < K / 8u; i += 32u)
+                    row[i] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
                 u32 *row32 = reinterpret_cast<u32 *>(sm.cnt[w]);
                 for (u32 i = lane; i < K / 2u; i += 32u)
                     row32[i] = 0;
@@ -484,7 +461,44 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
             const u32 per = K > THREADS ? K / THREADS : 1u;
             const u32 v0 = tid * per;
             u32 part = 0;
-            if (v0 < K) {
+            if (per == 2u) {
+                // two adjacent values per thread: their counters of every warp
+                // in one 32-bit word
+                u32 s_lo = 0, s_hi = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; ++w2) {
+                    u32 *c2 = reinterpret_cast<u32 *>(&sm.cnt[w2][v0]);
+                    const u32 c = *c2;
+                    *c2 = s_lo | (s_hi << 16);
+                    s_lo += c & 0xffffu;
+                    s_hi += c >> 16;
+                }
+                if (v0 + 1u == K - 1u)
+                    s_hi -= T - m;  // the padding elements
+                sm.tstart[v0] = s_lo;  // the totals, for now
+                sm.tstart[v0 + 1u] = s_hi;
+                part = s_lo + s_hi;
+            } else if (per == 4u) {
+                // four adjacent values per thread: their counters of every
+                // warp in one 64-bit word
+                u32 sv[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int w2 = 0; w2 < NW; ++w2) {
+                    u64 *c4 = reinterpret_cast<u64 *>(&sm.cnt[w2][v0]);
+                    const u64 c = *c4;
+                    *c4 = (u64)sv[0] | ((u64)sv[1] << 16) | ((u64)sv[2] << 32) | ((u64)sv[3] << 48);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        sv[i] += (u32)(c >> (16 * i)) & 0xffffu;
+                }
+                if (v0 + 3u == K - 1u)
+                    sv[3] -= T - m;  // the padding elements
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    sm.tstart[v0 + i] = sv[i];  // the totals, for now
+                    part += sv[i];
+                }
+            } else if (v0 < K) {
                 for (u32 i = 0; i < per; ++i) {
                     const u32 d = v0 + i;
                     u32 s2 = 0;
@@ -533,14 +547,30 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                 const u32 e = w * 32u * E + (u32)q * 32u + lane;
                 if (e < m) {
                     const u32 d = dr[q] & 0xffffu;
-                    sm.perm[sm.tstart[d] + sm.cnt[w][d] + (dr[q] >> 16)] = e | (d << 16);
+                    sm.perm[sm.tstart[d] + sm.cnt[w][d] + (dr[q] >> 16)] =
+                        (typename Sm::PermT)(P16 ? e : (e | (d << 16)));
                 }
             }
             __syncthreads();
             // every value's records leave as one contiguous run
             for (u32 s = tid; s < m; s += THREADS) {
                 const u32 pe = sm.perm[s];
-                copy_record<RW>(dst + (sm.goff[pe >> 16] + s) * rw, recs + (u64)(pe & 0xffffu) * rw, rw);
+                if constexpr (P16) {
+                    const u64 *r = recs + (u64)pe * rw;
+                    if constexpr (RW == 2) {
+                        const uint4 x = *reinterpret_cast<const uint4 *>(r);  // the record, once
+                        const u64 w0v = ((u64)x.y << 32) | x.x, w1v = ((u64)x.w << 32) | x.z;
+                        const u64 lw = g.win.wl ? w1v : w0v, hw = g.win.wh ? w1v : w0v;
+                        const u32 d = digit_from(g, lw, hw, model);
+                        *reinterpret_cast<uint4 *>(dst + (sm.goff[d] + s) * 2u) = x;
+                    } else {
+                        const u64 lw = r[g.win.wl];
+                        const u32 d = digit_from(g, lw, g.win.wh != g.win.wl ? r[g.win.wh] : lw, model);
+                        copy_record<RW>(dst + (sm.goff[d] + s) * rw, r, rw);
+                    }
+                } else {
+                    copy_record<RW>(dst + (sm.goff[pe >> 16] + s) * rw, recs + (u64)(pe & 0xffffu) * rw, rw);
+                }
             }
             if (tid == 0)
                 atomicAdd(&ctrs->scatter_bytes, 2ull * m * rw * 8u);
@@ -570,8 +600,9 @@ namespace {
 
 constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
 
-// distribution variants: {id, threads, E, RW, KM, NB}; 5-8 fit two CTAs on
-// an SM (5-7 take digits of at most 8 bits, 8 smaller tiles)
+// distribution variants: {id, threads, E, RW, KM, NB}; 5-10 fit two CTAs on
+// an SM (5-7 take digits of at most 8 bits, 9 of 9 bits; 8 and 10 keep a
+// 16-bit permutation, 8 with smaller tiles, 10 with fewer, longer warps)
 #define WSCATTER_VARIANTS(X)            \
     X(0, 512, 8, 1, KMAX, 2)            \
     X(1, 512, 8, 2, KMAX, 2)            \
@@ -581,7 +612,9 @@ constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
     X(5, 512, 8, 2, 256, 1)             \
     X(6, 512, 8, 1, 256, 1)             \
     X(7, 512, 4, 4, 256, 1)             \
-    X(8, 512, 4, 2, KMAX, 1)
+    X(8, 512, 4, 2, KMAX, 1)            \
+    X(9, 512, 8, 2, 512, 1)             \
+    X(10, 256, 16, 2, KMAX, 1)
 
 template <int THREADS, int E, int RW, int KM, int NB>
 cudaError_t prepare_wscatter(u32 rw, size_t *smem)
