@@ -11,11 +11,14 @@
  * records with equal keys keep their input order, so the output is unique and
  * is moved bit for bit.
  *
- * Method (Sec. 3.1-3.4): MSD radix sort with radix 256.  Each pass over a bin
- * builds a digit histogram, turns it into bin offsets with an exclusive prefix
- * (Sec. 1), and distributes whole records stably; big bins recurse with more
- * passes (Sec. 3.3), small bins are finished by an on-chip sort (Sec. 3.4,
- * 3.5).  Digits that are constant within a bin are skipped without moving data.
+ * Method (Sec. 3.1-3.4): MSD radix sort.  Each pass over a bin builds a digit
+ * histogram, turns it into bin offsets with an exclusive prefix (Sec. 1), and
+ * distributes whole records stably; big bins recurse with more passes (Sec.
+ * 3.3), small bins are finished by an on-chip sort (Sec. 3.4, 3.5).  The paper
+ * uses radix 256 (Sec. 3.1); here a digit is a window of 8 to 10 key bits
+ * picked per bin from its size, so that two passes bring 2^31 uniform records
+ * down to bins that one SM sorts in shared memory.  Key bits that are constant
+ * within a bin are skipped without moving data.
  *
  * Conventions for every call below:
  *  - Pointers named d_* and the record buffers `in`/`tmp` are DEVICE pointers
@@ -68,7 +71,7 @@ enum {
     RADULS_K_PLAN = 2,      /* prefix sums and sub-bin classification (Fig. 1-3 on the GPU) */
     RADULS_K_SCATTER = 3,   /* stable distribution of big bins (second traversal, Sec. 1) */
     RADULS_K_COPY = 4,      /* copy-back of finished bins left in tmp */
-    RADULS_K_BLOCK = 5,     /* on-chip sorts of small-bin runs (Sec. 3.4-3.5) */
+    RADULS_K_BLOCK = 5,     /* on-chip sorts of small bins and runs of them (Sec. 3.4-3.5) */
     RADULS_K_LEARNED = 6,   /* learned-partition fit, count and distribution */
     RADULS_K_BATCHED = 7,   /* persistent batched segmented sort */
     RADULS_K_BUCKET = 8,    /* mid-size bins: split by one CTA and sorted on chip through L2 (Sec. 3.4) */
@@ -251,7 +254,8 @@ int raduls_histogram(const void *in, uint64_t n_recs, uint32_t rec_bytes, uint32
 /* One stable distribution pass on digit `digit` over the whole array, `in` ->
  * `out` (device, n_recs*rec_bytes each, not overlapping): the histogram, the
  * exclusive prefix and the stable scatter of Sec. 1 done by the GPU pass
- * kernels (tile ranking + single-pass look-back scan). */
+ * kernels (chunk histograms chained by a single-pass look-back, then a
+ * scatter whose tiles are ranked and regrouped in shared memory). */
 int raduls_distribution_pass(const void *in, void *out, uint64_t n_recs, uint32_t rec_bytes,
                              uint32_t key_bytes, uint32_t digit, void *stream);
 
@@ -290,22 +294,25 @@ typedef struct {
     uint32_t bin_sort;         /* 1: small bins go to the streamed on-chip sort first */
 } raduls_tuning;
 
-/* Autotuner of the launch shapes and size-class thresholds (the paper has no
- * counterpart; its scheduling constants, Sec. 3.2-3.5, are CPU-specific).
- * Fills `in` with seeded uniform records (SplitMix64 words), sorts them once
- * per candidate setting -- every distribution tile shape that fits the
- * record width, the on-chip class at its full and half capacity, the
- * mid-size class off, at half and at full size -- with `tmp` as scratch,
- * times each with CUDA events (best of two), and keeps the fastest for later
- * calls on this device with this record width (candidates go from the default
- * shape outward, and one must beat the current choice by more than 1% to
- * replace it, so timing noise never trades the default size classes for
- * smaller ones that only uniform keys tolerate): plain sorts when
- * d_seg_offsets is NULL, batched sorts (with those offsets) otherwise.  The
- * digit width stays 8 bits.  `in` and `tmp` hold n_recs records; their
- * contents are undefined afterwards.  Synchronises `stream`; not for use
- * inside a stream capture.  `out` may be NULL.  Environment overrides
- * (RADULS_SCATTER_VARIANT, RADULS_BUCKET_MAX) still take precedence. */
+/* Autotuner of the launch shapes, digit widths and size-class thresholds
+ * (the paper has no counterpart; its scheduling constants, Sec. 3.2-3.5, are
+ * CPU-specific).  Fills `in` with seeded uniform records (SplitMix64 words),
+ * sorts them once per candidate setting -- every distribution tile shape
+ * that fits the record width, the widest digit at 8, 9 and 10 bits, two
+ * sub-bin size targets, the on-chip class at its full and half capacity, the
+ * streamed on-chip bin sort on and off, the mid-size class off, at half and
+ * at full size -- with `tmp` as scratch, times each with CUDA events (best of
+ * two), and keeps the fastest for later calls on this device with this record
+ * width (candidates go from the default shape outward, and the winner must
+ * beat the default by more than 1% in a final alternating re-timing, so
+ * timing noise never trades the default for a setting that only uniform keys
+ * tolerate): plain sorts when d_seg_offsets is NULL, batched sorts (with those
+ * offsets) otherwise.  `in` and `tmp` hold n_recs records; their contents are
+ * undefined afterwards.  Synchronises `stream`; not for use inside a stream
+ * capture.  `out` may be NULL.  Environment overrides still take precedence:
+ * RADULS_SCATTER_VARIANT (one distribution shape for every level),
+ * RADULS_WMAX (widest digit, 8..10), RADULS_LEAF (sub-bin size target),
+ * RADULS_BLOCK_CAP, RADULS_BUCKET_MAX, RADULS_BIN_SORT (0/1). */
 int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                     const uint64_t *d_seg_offsets, uint32_t n_segs, raduls_tuning *out, void *stream);
 

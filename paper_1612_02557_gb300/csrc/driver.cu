@@ -184,7 +184,7 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
             const u32 bcap = binsort_cap_of(bv);
             s.cap_b = (t.valid && t.cap_b > WARP_BIN && t.cap_b < bcap) ? t.cap_b : bcap;
             if (s.leaf == 0)
-                s.leaf = s.cap_b / 5u * 4u;  // bins of about 4/5 of the capacity: the largest still fit
+                s.leaf = s.cap_b / 10u * 9u;  // sub-bins of about 9/10 of the capacity: the largest still fit
         }
     }
     s.tile_s = wscatter_tile_of(s.scat_var);
@@ -786,6 +786,7 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             a.caps = L.caps;  // the level's buffers fix the distribution tile capacity
             a.status = B.status;
             const Model *model = learned ? c.mdl.model : nullptr;
+            bool model_pass = false;  // this level distributes on the model's bucket
             TIMED(RADULS_K_SETUP, launch_prep(B.hist, B.orand, wk.ctrs, n_grid, j.hist_out ? 1u : 0u, st));
             if (j.hist_out) {
                 // histogram only (raduls_histogram): one traversal, counts per value
@@ -832,6 +833,7 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
                                                           B.status, B.orand, wk.ctrs, c.mdl.model, wk.epoch,
                                                           c.wait_ns, ~0u, st));
                         model = c.mdl.model;
+                        model_pass = true;
                     }
                     // else: the plain passes go on from this level's histogram of the top byte
                 }
@@ -844,8 +846,8 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
             // the level's shape for its widest digit; the learned pass needs
             // one that takes 2^log2b values
             Shape sl = s;
-            sl.scat_var = level_scatter_variant(s, model ? log2b : lvl_w);
-            if (model && ((u64)1 << log2b) > wscatter_kmax_of(sl.scat_var))
+            sl.scat_var = level_scatter_variant(s, model_pass ? log2b : lvl_w);
+            if (model_pass && ((u64)1 << log2b) > wscatter_kmax_of(sl.scat_var))
                 sl.scat_var = wide_scatter_variant(j.rw);
             TIMED(RADULS_K_SCATTER, launch_wscatter(sl, j.in, j.tmp, L.scat, B.tile_scat, L.cell[cur], B.status,
                                                     wk.ctrs, model, c.wait_ns, st));
