@@ -88,16 +88,20 @@ WORKLOADS = {
 # moved, per kernel class, from one capture of the current kernels on uniform
 # 16-byte records.  A class missing here has no capture of its current code.
 DRAM_BYTES_PER_RECORD = {
-    "scatter": (1.096136e9 + 1.048401e9) / 2 ** 26,   # ncu capture of scatter_kernel, 2^26 records
-    "bucket": (566.772736e6 + 414.964224e6) / 1e7,    # ncu capture of bucket_kernel, 10^7 records
+    # wscatter_kernel, 10-bit digits (variant 10), both launches of a 2^27-record sort
+    "scatter": (2.605682e9 + 2.474924e9 + 2.428163e9 + 2.327375e9) / 2 / 2 ** 27,
+    # bin_sort_kernel, 2^27 records in ~2,048-record bins
+    "block": (2.149775e9 + 2.090046e9) / 2 ** 27,
+    # bucket_kernel, 10^7 records in 256 mid-size bins
+    "bucket": (565.243136e6 + 414.964992e6) / 1e7,
 }
 # stats field holding each class's algorithmic bytes (read + write of every record it moves)
 CLASS_BYTES = {"scatter": "scatter_bytes", "bucket": "bucket_bytes", "block": "block_bytes",
                "hist": "hist_bytes_read"}
-CLASS_KERNEL = {"scatter": "scatter_kernel (MSD distribution pass of big bins)",
+CLASS_KERNEL = {"scatter": "wscatter_kernel (MSD distribution pass of big bins)",
                 "bucket": "bucket_kernel (mid-size bins, one CTA each)",
-                "block": "block_sort_kernel (on-chip sorts of small bins)",
-                "hist": "hist_kernel (digit histograms of big bins)"}
+                "block": "bin_sort_kernel (streamed on-chip sort of small bins; block_sort_kernel takes what it leaves)",
+                "hist": "whist_kernel (chunk histograms chained by look-back)"}
 
 
 def roofline_of(kernel_ms: dict, cls_bytes: dict, cls_launches: dict, steps: int, rec: int, hbm_peak: float,
