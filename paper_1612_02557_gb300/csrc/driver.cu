@@ -104,7 +104,11 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     // mid-size bins: one CTA sorts a bin of up to BUCKET_BYTES through L2
     constexpr u32 BUCKET_BYTES = 640u * 1024u;
     s.bucket_var = rw == 1 ? 0 : rw == 2 ? 1 : rw == 4 ? 2 : -1;
-    s.bucket_max = s.bucket_var < 0 ? 0u : BUCKET_BYTES / (rw * 8u);
+    // Plain sorts leave the class off by default: another distribution pass
+    // and the on-chip kernels finish such bins faster (skewed 2^30 x 16 B:
+    // 82.7 against 86.4 ms; 2^28 x 32 B with 16-byte keys: 46.9 against 52.7
+    // ms); batched sorts keep it for their mid-size arrays.
+    s.bucket_max = (s.bucket_var < 0 || !batched) ? 0u : BUCKET_BYTES / (rw * 8u);
     // tuned settings (raduls_autotune), else the defaults above
     Tuned t{};
     if (g_force) {
@@ -1751,8 +1755,12 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
         t.leaf = 0;
         time_one(t, ms);
     }
-    const u32 bmaxes[2] = {base.bucket_max / 2u, 0u};
-    for (int bi = 0; bi < 2 && base.bucket_max && rc == RADULS_OK; ++bi) {
+    // the mid-size class: at half size and off when it is on by default, at
+    // full and half size when it is off
+    const u32 bfull = base.bucket_var < 0 ? 0u : 640u * 1024u / (rw * 8u);
+    const u32 bmaxes[2] = {base.bucket_max ? base.bucket_max / 2u : (bfull < BUCKET_IDX_MAX ? bfull : BUCKET_IDX_MAX),
+                           base.bucket_max ? 0u : bfull / 2u};
+    for (int bi = 0; bi < 2 && base.bucket_var >= 0 && rc == RADULS_OK; ++bi) {
         Tuned t = best;
         t.bucket_max = bmaxes[bi] > t.cap_b ? bmaxes[bi] : 0u;
         if (t.bucket_max == best.bucket_max)

@@ -6,8 +6,9 @@ and at later levels, runs of small sub-bins, single sub-bins sorted by the
 whole CTA, sub-bins too big for shared memory that go on to the next level,
 bins whose last digit is split (no digit left after it) from either buffer,
 and heavy duplicates (with 8-bit digits in every distribution pass, as the
-inputs are built around them).  The same inputs sorted with the path switched
-off (RADULS_BUCKET_MAX=0) must give the same bytes.
+inputs are built around them, and the class switched on: plain sorts leave it
+off by default).  The same inputs sorted with the path switched off
+(RADULS_BUCKET_MAX=0) must give the same bytes.
 """
 from __future__ import annotations
 
@@ -33,14 +34,17 @@ def _cuda():
 @pytest.fixture(scope="module", autouse=True)
 def _byte_digits():
     """8-bit digits in every distribution pass, so that the bins these inputs
-    are built around (and the mid-size class) occur as described."""
-    old = os.environ.get("RADULS_WMAX")
-    os.environ["RADULS_WMAX"] = "8"
+    are built around occur as described, and the mid-size class switched on
+    (plain sorts leave it off by default) for bins of up to 640 KB."""
+    want = {"RADULS_WMAX": "8", "RADULS_BUCKET_MAX": "40960"}
+    old = {k: os.environ.get(k) for k in want}
+    os.environ.update(want)
     yield
-    if old is None:
-        del os.environ["RADULS_WMAX"]
-    else:
-        os.environ["RADULS_WMAX"] = old
+    for k, v in old.items():
+        if v is None:
+            del os.environ[k]
+        else:
+            os.environ[k] = v
 
 
 def _set_byte(keys: np.ndarray, byte: int, values: np.ndarray) -> None:
@@ -94,10 +98,10 @@ def _with_env(name: str, value: str, fn):
 
 
 def _sort_both_ways(recs: np.ndarray, key_bytes: int):
-    """The default settings and the mid-size path switched off (RADULS_BUCKET_MAX=0)."""
+    """The mid-size path on (the module's setting) and switched off (RADULS_BUCKET_MAX=0)."""
     got = gpu_sort(recs, key_bytes)
     off = _with_env("RADULS_BUCKET_MAX", "0", lambda: gpu_sort(recs, key_bytes))
-    return {"default": got, "off": off}
+    return {"on": got, "off": off}
 
 
 @pytest.mark.parametrize("rec_bytes,key_bytes", [(8, 8), (16, 8), (32, 16), (24, 8), (16, 16)])
