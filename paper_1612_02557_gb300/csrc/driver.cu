@@ -38,6 +38,7 @@ bool scatter_variant_fits(int v, u32 rw)
     case 8:
     case 9:
     case 10:
+    case 11:
         return rw == 2;
     case 6:
         return rw == 1;
@@ -88,7 +89,7 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     } else if (rw == 2) {
         // plain sorts: digits of up to 10 bits, two CTAs per SM; batched sorts
         // keep 8-bit digits (their arrays are mostly below one chunk)
-        s.scat_var = batched ? 5 : 10;
+        s.scat_var = batched ? 5 : 11;
         s.block_var = 1;
     } else if (rw == 4) {
         s.scat_var = 7;
@@ -159,8 +160,11 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
         }
     }
     // plain sorts of 16-byte records: each level takes the two-CTA shape made
-    // for its widest digit (variant 5: 8 bits, 9: 9 bits, 10: 10 bits)
-    s.scat_by_width = rw == 2 && !batched && (s.scat_var == 9 || s.scat_var == 10);
+    // for its widest digit (variant 5: 8 bits, 9: 9 bits, 11 (or 10): 10 bits)
+    s.scat_by_width = rw == 2 && !batched && (s.scat_var == 9 || s.scat_var == 10 || s.scat_var == 11);
+    s.scat_var10 = s.scat_var == 10 ? 10 : 11;
+    if (const char *v = getenv("RADULS_SCATTER10"))  // the 10-bit levels' shape (10 or 11)
+        s.scat_var10 = atoi(v) == 11 ? 11 : 10;
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
         if (scatter_variant_fits(want, rw)) {
@@ -209,7 +213,7 @@ int level_scatter_variant(const Shape &s, u32 w)
 {
     if (!s.scat_by_width)
         return s.scat_var;
-    return w <= 8u ? 5 : w == 9u ? 9 : 10;
+    return w <= 8u ? 5 : w == 9u ? 9 : s.scat_var10;
 }
 
 namespace {
@@ -1705,7 +1709,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     }
     time_one(best, ms);
     const Tuned base_t = best;
-    for (int v = 0; v < 11 && rc == RADULS_OK; ++v) {
+    for (int v = 0; v < 12 && rc == RADULS_OK; ++v) {
         if (v == base.scat_var || !scatter_variant_fits(v, rw) || ((v == 3 || v == 4) && rw <= 4))
             continue;
         Tuned t = best;

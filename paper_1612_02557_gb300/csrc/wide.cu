@@ -263,8 +263,7 @@ struct WScatterSmem {
     static constexpr int NW = THREADS / 32;
     using PermT = typename std::conditional<P16, unsigned short, u32>::type;
     unsigned short cnt[NW][KM];       // per warp: records of each value in the tile, then its offsets
-    u64 cursor[KM];                   // next global position of every value in this chunk
-    u64 goff[KM];                     // global position of sorted slot 0's value run, per value
+    u32 goff[KM];                     // position of sorted slot 0's value run, per value, from the bin's start
     u32 tstart[KM];                   // first sorted slot of every value in the tile
     PermT perm[THREADS * E];          // sorted slot -> element (| value << 16 unless P16)
     u32 wsum[NW];
@@ -301,6 +300,7 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
 {
     constexpr u32 T = THREADS * E;
     constexpr int NW = THREADS / 32;
+    constexpr u32 CPT = KM > THREADS ? (u32)KM / THREADS : 1u;  // digit values (cursors) per thread
     static_assert(T <= 65536, "tile slots are 16-bit");
     static_assert(KM <= 65536 && KM <= (int)KMAX, "values are 16-bit");
     static_assert(E * 32 <= 65535, "per-warp counts are 16-bit");
@@ -360,14 +360,23 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
         const u64 c_hi = min(item.begin + item.count, c_lo + tile_h);
         const u64 *src = (item.flags & ITEM_IN_TMP) ? tmp : in;
         u64 *dst = (item.flags & ITEM_IN_TMP) ? in : tmp;
-        // cursors: sub-bin starts (the planner left them in the bin's last
-        // chunk row) plus what the bin's earlier chunks hold of each value
+        // this thread's values [v0, v0 + per) and their cursors (registers):
+        // sub-bin starts (the planner left them in the bin's last chunk row)
+        // plus what the bin's earlier chunks hold of each value
+        const u32 per = K > THREADS ? K / THREADS : 1u;
+        const u32 v0 = tid * per;
+        u64 cur[CPT];
         {
             const u64 *st = status + cell_off[item.row];
             const u32 nch = ceil_div_u64(item.count, tile_h);
             const u64 *starts = st + (u64)(nch - 1u) * K;
-            for (u32 d = tid; d < K; d += THREADS)
-                sm.cursor[d] = starts[d] + (j > 0 ? (ld_relaxed_u64(&st[(u64)(j - 1u) * K + d]) & LB_VAL_MASK) : 0ull);
+#pragma unroll
+            for (u32 i = 0; i < CPT; ++i) {
+                const u32 d = v0 + i;
+                cur[i] = (i < per && d < K)
+                             ? starts[d] + (j > 0 ? (ld_relaxed_u64(&st[(u64)(j - 1u) * K + d]) & LB_VAL_MASK) : 0ull)
+                             : 0ull;
+            }
         }
         const u32 n_sub = (u32)((c_hi - c_lo + T - 1) / T);
         if (tid == 0 && !sm.abort && n_sub > 0) {
@@ -458,8 +467,6 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
             }
             __syncthreads();
             // per-warp offsets and tile totals of this thread's values [v0, v0 + per)
-            const u32 per = K > THREADS ? K / THREADS : 1u;
-            const u32 v0 = tid * per;
             u32 part = 0;
             if (per == 2u) {
                 // two adjacent values per thread: their counters of every warp
@@ -531,15 +538,19 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                     run += sm.wsum[w2];
                 // each value's run starts at slot `run` of the sorted tile and at
                 // its cursor in the bin; the cursor then moves past the run
-                if (v0 < K)
-                    for (u32 i = 0; i < per; ++i) {
-                        const u32 d = v0 + i, tot = sm.tstart[d];
-                        const u64 cur = sm.cursor[d];
+#pragma unroll
+                for (u32 i = 0; i < CPT; ++i) {
+                    const u32 d = v0 + i;
+                    if (i < per && d < K) {
+                        const u32 tot = sm.tstart[d];
                         sm.tstart[d] = run;
-                        sm.goff[d] = cur - run;
-                        sm.cursor[d] = cur + tot;
+                        // relative to the bin's start, modulo 2^32: slot s of
+                        // the run lands at begin + (goff + s), which is inside the bin
+                        sm.goff[d] = (u32)(cur[i] - run - item.begin);
+                        cur[i] += tot;
                         run += tot;
                     }
+                }
             }
             __syncthreads();
 #pragma unroll
@@ -562,14 +573,15 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                         const u64 w0v = ((u64)x.y << 32) | x.x, w1v = ((u64)x.w << 32) | x.z;
                         const u64 lw = g.win.wl ? w1v : w0v, hw = g.win.wh ? w1v : w0v;
                         const u32 d = digit_from(g, lw, hw, model);
-                        *reinterpret_cast<uint4 *>(dst + (sm.goff[d] + s) * 2u) = x;
+                        *reinterpret_cast<uint4 *>(dst + (item.begin + (u32)(sm.goff[d] + s)) * 2u) = x;
                     } else {
                         const u64 lw = r[g.win.wl];
                         const u32 d = digit_from(g, lw, g.win.wh != g.win.wl ? r[g.win.wh] : lw, model);
-                        copy_record<RW>(dst + (sm.goff[d] + s) * rw, r, rw);
+                        copy_record<RW>(dst + (item.begin + (u32)(sm.goff[d] + s)) * rw, r, rw);
                     }
                 } else {
-                    copy_record<RW>(dst + (sm.goff[pe >> 16] + s) * rw, recs + (u64)(pe & 0xffffu) * rw, rw);
+                    copy_record<RW>(dst + (item.begin + (u32)(sm.goff[pe >> 16] + s)) * rw,
+                                    recs + (u64)(pe & 0xffffu) * rw, rw);
                 }
             }
             if (tid == 0)
@@ -600,9 +612,10 @@ namespace {
 
 constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
 
-// distribution variants: {id, threads, E, RW, KM, NB}; 5-10 fit two CTAs on
-// an SM (5-7 take digits of at most 8 bits, 9 of 9 bits; 8 and 10 keep a
-// 16-bit permutation, 8 with smaller tiles, 10 with fewer, longer warps)
+// distribution variants: {id, threads, E, RW, KM, NB}; 5-11 fit two CTAs on
+// an SM (5-7 take digits of at most 8 bits, 9 of 9 bits; 8, 10 and 11 keep a
+// 16-bit permutation: 8 with smaller tiles, 10 with fewer, longer warps, 11
+// the 512 x 8 tile of the others)
 #define WSCATTER_VARIANTS(X)            \
     X(0, 512, 8, 1, KMAX, 2)            \
     X(1, 512, 8, 2, KMAX, 2)            \
@@ -614,7 +627,8 @@ constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
     X(7, 512, 4, 4, 256, 1)             \
     X(8, 512, 4, 2, KMAX, 1)            \
     X(9, 512, 8, 2, 512, 1)             \
-    X(10, 256, 16, 2, KMAX, 1)
+    X(10, 256, 16, 2, KMAX, 1)          \
+    X(11, 512, 8, 2, KMAX, 1)
 
 template <int THREADS, int E, int RW, int KM, int NB>
 cudaError_t prepare_wscatter(u32 rw, size_t *smem)

@@ -22,7 +22,7 @@ def _cuda():
     lib()
 
 
-@pytest.mark.parametrize("variant", [1, 5, 8, 9, 10])
+@pytest.mark.parametrize("variant", [1, 5, 8, 9, 10, 11])
 def test_each_distribution_shape_matches_oracle(oracle_mod, variant):
     recs = datagen.random_records(3_000_001, 16, 8, 77)
     old = os.environ.get("RADULS_SCATTER_VARIANT")
@@ -46,7 +46,7 @@ def test_tuned_settings_keep_parity(oracle_mod):
         b = scratch(n, 2)
         t = p.raduls_autotune(a, b, n, 16, 8)
         assert t["candidates"] >= 2 and t["best_ms"] > 0
-        assert t["block_cap"] in (2048, 2560, 4096, 5120, 8192) and t["scatter_variant"] in (1, 5, 8, 9, 10)
+        assert t["block_cap"] in (2048, 2560, 4096, 5120, 8192) and t["scatter_variant"] in (1, 5, 8, 9, 10, 11)
         assert 8 <= t["digit_bits"] <= 10 and 0 < t["leaf"] <= t["block_cap"] and t["bin_sort"] in (0, 1)
         for size in (1 << 21, 3_000_001):
             recs = datagen.random_records(size, 16, 8, size)
