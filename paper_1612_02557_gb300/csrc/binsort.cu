@@ -562,7 +562,10 @@ bin_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkIte
 namespace {
 
 // streamed bin sort variants: {id, threads, CAP (records), RW}
-#define BINSORT_VARIANTS(X) X(0, 1024, 5120, 2) X(1, 512, 5120, 2)
+// (8-byte records have none: their bins of up to 4,096 records -- the general
+// kernel's capacity -- sort faster through the mid-size class, 42.8 against
+// 46.0 ms for 2^30 records)
+#define BINSORT_VARIANTS(X) X(0, 1024, 5120, 2) X(1, 512, 5120, 2) X(3, 1024, 2048, 4)
 
 template <int THREADS, int CAP, int RW>
 cudaError_t prepare_binsort(size_t *smem)

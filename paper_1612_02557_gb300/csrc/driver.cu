@@ -41,7 +41,12 @@ bool scatter_variant_fits(int v, u32 rw)
     case 11:
         return rw == 2;
     case 6:
+    case 12:
+    case 13:
         return rw == 1;
+    case 14:
+    case 15:
+        return rw == 4;
     case 2:
     case 7:
         return rw == 4;
@@ -92,7 +97,7 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
         s.scat_var = batched ? 5 : 11;
         s.block_var = 1;
     } else if (rw == 4) {
-        s.scat_var = 7;
+        s.scat_var = batched ? 7 : 15;
         s.block_var = 2;
     } else if (rw <= 8) {
         s.scat_var = 3;
@@ -105,11 +110,11 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     // mid-size bins: one CTA sorts a bin of up to BUCKET_BYTES through L2
     constexpr u32 BUCKET_BYTES = 640u * 1024u;
     s.bucket_var = rw == 1 ? 0 : rw == 2 ? 1 : rw == 4 ? 2 : -1;
-    // Plain sorts leave the class off by default: another distribution pass
-    // and the on-chip kernels finish such bins faster (skewed 2^30 x 16 B:
-    // 82.7 against 86.4 ms; 2^28 x 32 B with 16-byte keys: 46.9 against 52.7
-    // ms); batched sorts keep it for their mid-size arrays.
-    s.bucket_max = (s.bucket_var < 0 || !batched) ? 0u : BUCKET_BYTES / (rw * 8u);
+    // Plain sorts of record widths with a streamed on-chip sort leave the
+    // class off by default: wider digits and that sort finish such bins
+    // faster (skewed 2^30 x 16 B: 82.7 against 86.4 ms); batched sorts keep
+    // it for their mid-size arrays.
+    s.bucket_max = (s.bucket_var < 0 || (!batched && binsort_variant_for(rw) >= 0)) ? 0u : BUCKET_BYTES / (rw * 8u);
     // tuned settings (raduls_autotune), else the defaults above
     Tuned t{};
     if (g_force) {
@@ -161,10 +166,13 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     }
     // plain sorts of 16-byte records: each level takes the two-CTA shape made
     // for its widest digit (variant 5: 8 bits, 9: 9 bits, 11 (or 10): 10 bits)
-    s.scat_by_width = rw == 2 && !batched && (s.scat_var == 9 || s.scat_var == 10 || s.scat_var == 11);
-    s.scat_var10 = s.scat_var == 10 ? 10 : 11;
-    if (const char *v = getenv("RADULS_SCATTER10"))  // the 10-bit levels' shape (10 or 11)
-        s.scat_var10 = atoi(v) == 11 ? 11 : 10;
+    s.scat_by_width = !batched && ((rw == 2 && (s.scat_var == 9 || s.scat_var == 10 || s.scat_var == 11)) ||
+                                   (rw == 1 && (s.scat_var == 12 || s.scat_var == 13)) ||
+                                   (rw == 4 && (s.scat_var == 14 || s.scat_var == 15)));
+    s.scat_var10 = rw == 1 ? 13 : rw == 4 ? 15 : (s.scat_var == 10 ? 10 : 11);
+    if (const char *v = getenv("RADULS_SCATTER10"))  // the 10-bit levels' shape of 16-byte records (10 or 11)
+        if (rw == 2)
+            s.scat_var10 = atoi(v) == 11 ? 11 : 10;
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
         if (scatter_variant_fits(want, rw)) {
@@ -186,9 +194,10 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
         if (const char *v = getenv("RADULS_BIN_VARIANT"))
             if (bv >= 0 && binsort_rw_of(atoi(v)) == rw)
                 bv = atoi(v);
-        if (want == 1 && bv >= 0 && rw == 2) {
+        if (want == 1 && bv >= 0) {
             s.bins_var = bv;
-            s.block_var = 5;
+            if (rw == 2)
+                s.block_var = 5;  // the general kernel that takes what it leaves holds as many records
             const u32 bcap = binsort_cap_of(bv);
             s.cap_b = (t.valid && t.cap_b > WARP_BIN && t.cap_b < bcap) ? t.cap_b : bcap;
             if (s.leaf == 0)
@@ -213,7 +222,8 @@ int level_scatter_variant(const Shape &s, u32 w)
 {
     if (!s.scat_by_width)
         return s.scat_var;
-    return w <= 8u ? 5 : w == 9u ? 9 : s.scat_var10;
+    const int v8 = s.rw == 1 ? 6 : s.rw == 4 ? 7 : 5, v9 = s.rw == 1 ? 12 : s.rw == 4 ? 14 : 9;
+    return w <= 8u ? v8 : w == 9u ? v9 : s.scat_var10;
 }
 
 namespace {
@@ -1709,7 +1719,7 @@ int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, ui
     }
     time_one(best, ms);
     const Tuned base_t = best;
-    for (int v = 0; v < 12 && rc == RADULS_OK; ++v) {
+    for (int v = 0; v < 16 && rc == RADULS_OK; ++v) {
         if (v == base.scat_var || !scatter_variant_fits(v, rw) || ((v == 3 || v == 4) && rw <= 4))
             continue;
         Tuned t = best;

@@ -612,10 +612,10 @@ namespace {
 
 constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
 
-// distribution variants: {id, threads, E, RW, KM, NB}; 5-11 fit two CTAs on
-// an SM (5-7 take digits of at most 8 bits, 9 of 9 bits; 8, 10 and 11 keep a
-// 16-bit permutation: 8 with smaller tiles, 10 with fewer, longer warps, 11
-// the 512 x 8 tile of the others)
+// distribution variants: {id, threads, E, RW, KM, NB}; 5-15 fit two CTAs on
+// an SM (5-7 take digits of at most 8 bits, 9, 12 and 14 of 9 bits; those of
+// 10 bits keep a 16-bit permutation: 8 with smaller tiles, 10 with fewer,
+// longer warps, 11, 13 and 15 the tile of the 8-bit shape of their width)
 #define WSCATTER_VARIANTS(X)            \
     X(0, 512, 8, 1, KMAX, 2)            \
     X(1, 512, 8, 2, KMAX, 2)            \
@@ -628,7 +628,11 @@ constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
     X(8, 512, 4, 2, KMAX, 1)            \
     X(9, 512, 8, 2, 512, 1)             \
     X(10, 256, 16, 2, KMAX, 1)          \
-    X(11, 512, 8, 2, KMAX, 1)
+    X(11, 512, 8, 2, KMAX, 1)           \
+    X(12, 512, 8, 1, 512, 1)            \
+    X(13, 512, 8, 1, KMAX, 1)           \
+    X(14, 512, 4, 4, 512, 1)            \
+    X(15, 512, 4, 4, KMAX, 1)
 
 template <int THREADS, int E, int RW, int KM, int NB>
 cudaError_t prepare_wscatter(u32 rw, size_t *smem)

@@ -1,7 +1,7 @@
 """The streamed on-chip finisher (binsort.cu) against the oracle, bit for bit.
 
 Small bins (and runs of small sub-bins) are sorted in shared memory by a
-13-bit code count, a placement of (code, next 32 key bits, index) words and a
+13-bit code count, a placement of (code, next 38 key bits, index) words and a
 rank inside each code group; items with large groups of near-equal keys are
 handed to the general on-chip kernel.  Every case runs with the finisher on
 and off (RADULS_BIN_SORT), so both paths, and the hand-over between them, are
@@ -50,12 +50,13 @@ def _keys_from(words: np.ndarray, n: int, rw: int) -> np.ndarray:
 
 
 @pytest.mark.parametrize("on", [0, 1])
-@pytest.mark.parametrize("n", [2, 5119, 5121, 200_003, 3_000_017])
-def test_uniform_sizes(oracle_mod, on, n):
-    recs = datagen.random_records(n, 16, 8, 1000 + n)
+@pytest.mark.parametrize("n", [2, 2047, 4097, 5119, 5121, 200_003, 3_000_017])
+@pytest.mark.parametrize("rec_bytes,key_bytes", [(16, 8), (8, 8), (32, 8), (32, 16)])
+def test_uniform_sizes(oracle_mod, on, n, rec_bytes, key_bytes):
+    recs = datagen.random_records(n, rec_bytes, key_bytes, 1000 + n)
     with _env(RADULS_BIN_SORT=on):
-        got = gpu_sort(recs, 8)
-    np.testing.assert_array_equal(got, oracle_mod.sort(recs, 8, threads=8))
+        got = gpu_sort(recs, key_bytes)
+    np.testing.assert_array_equal(got, oracle_mod.sort(recs, key_bytes, threads=8))
 
 
 @pytest.mark.parametrize("on", [0, 1])
@@ -112,6 +113,19 @@ def test_digit_widths_feed_the_finisher(oracle_mod, on, wmax, leaf):
     with _env(**kw):
         got = gpu_sort(recs, 8)
     np.testing.assert_array_equal(got, oracle_mod.sort(recs, 8, threads=8))
+
+
+@pytest.mark.parametrize("rec_bytes", [8, 32])
+@pytest.mark.parametrize("distinct", [3, 5000])
+def test_near_equal_keys_other_widths(oracle_mod, rec_bytes, distinct):
+    rng = np.random.default_rng(distinct + rec_bytes)
+    n = 600_007
+    vals = rng.integers(0, 2**64, size=distinct, dtype=np.uint64)
+    keys = vals[rng.integers(0, distinct, size=n)]
+    recs = _keys_from(keys[:, None], n, rec_bytes // 8)
+    for on in (0, 1):
+        with _env(RADULS_BIN_SORT=on):
+            np.testing.assert_array_equal(gpu_sort(recs, 8), oracle_mod.sort(recs, 8, threads=8))
 
 
 def test_skewed_prefix_both_ways(oracle_mod):
