@@ -169,10 +169,18 @@ Shape choose_shape(u32 rw, u32 key_words, bool batched)
     s.scat_by_width = !batched && ((rw == 2 && (s.scat_var == 9 || s.scat_var == 10 || s.scat_var == 11)) ||
                                    (rw == 1 && (s.scat_var == 12 || s.scat_var == 13)) ||
                                    (rw == 4 && (s.scat_var == 14 || s.scat_var == 15)));
+    s.scat_var8 = rw == 1 ? 6 : rw == 4 ? 7 : 5;
+    s.scat_var9 = rw == 1 ? 12 : rw == 4 ? 14 : 9;
     s.scat_var10 = rw == 1 ? 13 : rw == 4 ? 15 : (s.scat_var == 10 ? 10 : 11);
-    if (const char *v = getenv("RADULS_SCATTER10"))  // the 10-bit levels' shape of 16-byte records (10 or 11)
-        if (rw == 2)
-            s.scat_var10 = atoi(v) == 11 ? 11 : 10;
+    // the shapes of 8-, 9- and 10-bit levels (when they follow the width)
+    const char *names[3] = {"RADULS_SCATTER8", "RADULS_SCATTER9", "RADULS_SCATTER10"};
+    int *slots[3] = {&s.scat_var8, &s.scat_var9, &s.scat_var10};
+    for (int i = 0; i < 3; ++i)
+        if (const char *v = getenv(names[i])) {
+            const int want = atoi(v);
+            if (scatter_variant_fits(want, rw) && wscatter_kmax_of(want) >= (256u << i))
+                *slots[i] = want;
+        }
     if (const char *v = getenv("RADULS_SCATTER_VARIANT")) {
         const int want = atoi(v);
         if (scatter_variant_fits(want, rw)) {
@@ -222,8 +230,7 @@ int level_scatter_variant(const Shape &s, u32 w)
 {
     if (!s.scat_by_width)
         return s.scat_var;
-    const int v8 = s.rw == 1 ? 6 : s.rw == 4 ? 7 : 5, v9 = s.rw == 1 ? 12 : s.rw == 4 ? 14 : 9;
-    return w <= 8u ? v8 : w == 9u ? v9 : s.scat_var10;
+    return w <= 8u ? s.scat_var8 : w == 9u ? s.scat_var9 : s.scat_var10;
 }
 
 namespace {

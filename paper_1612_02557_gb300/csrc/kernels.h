@@ -21,7 +21,7 @@ struct Shape {
     u32 wmax;        // widest digit of a distribution pass (bits, 8..WIDE_MAX)
     int bins_var;    // streamed on-chip finisher variant (-1: the general on-chip kernel alone)
     bool scat_by_width;  // each level's distribution shape follows its widest digit
-    int scat_var10;      // the shape of 10-bit levels when it does
+    int scat_var8, scat_var9, scat_var10;  // the shapes of 8-, 9- and 10-bit levels when it does
 };
 
 // The distribution shape of a level whose widest digit has w bits.
