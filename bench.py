@@ -88,8 +88,8 @@ WORKLOADS = {
 # moved, per kernel class, from one capture of the current kernels on uniform
 # 16-byte records.  A class missing here has no capture of its current code.
 DRAM_BYTES_PER_RECORD = {
-    # wscatter_kernel, 10-bit digits (variant 10), both launches of a 2^27-record sort
-    "scatter": (2.605682e9 + 2.474924e9 + 2.428163e9 + 2.327375e9) / 2 / 2 ** 27,
+    # wscatter_kernel, a 2^27-record sort split 10 bits (variant 11) then 9 bits (variant 9)
+    "scatter": (2.604236e9 + 2.472819e9 + 2.289581e9 + 2.208945e9) / 2 / 2 ** 27,
     # bin_sort_kernel, 2^27 records in ~2,048-record bins
     "block": (2.149775e9 + 2.090046e9) / 2 ** 27,
     # bucket_kernel, 10^7 records in 256 mid-size bins
