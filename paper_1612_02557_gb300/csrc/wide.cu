@@ -33,6 +33,11 @@
 
 #include "kernels.h"
 
+#ifndef RADULS_COPY_UNROLL
+#define RADULS_COPY_UNROLL 4
+#endif
+constexpr int COPY_UNROLL = RADULS_COPY_UNROLL;  // tile slots a thread writes at a time
+
 namespace raduls {
 
 namespace {
@@ -563,25 +568,39 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                 }
             }
             __syncthreads();
-            // every value's records leave as one contiguous run
-            for (u32 s = tid; s < m; s += THREADS) {
-                const u32 pe = sm.perm[s];
-                if constexpr (P16) {
-                    const u64 *r = recs + (u64)pe * rw;
-                    if constexpr (RW == 2) {
-                        const uint4 x = *reinterpret_cast<const uint4 *>(r);  // the record, once
-                        const u64 w0v = ((u64)x.y << 32) | x.x, w1v = ((u64)x.w << 32) | x.z;
-                        const u64 lw = g.win.wl ? w1v : w0v, hw = g.win.wh ? w1v : w0v;
-                        const u32 d = digit_from(g, lw, hw, model);
-                        *reinterpret_cast<uint4 *>(dst + (item.begin + (u32)(sm.goff[d] + s)) * 2u) = x;
+            // every value's records leave as one contiguous run; UC slots per
+            // thread at a time, so their shared-memory loads overlap
+            constexpr int UC = RW == 1 || RW == 2 ? COPY_UNROLL : 1;
+#pragma unroll
+            for (int q0 = 0; q0 < E; q0 += UC) {
+                u32 pe[UC];
+#pragma unroll
+                for (int u = 0; u < UC; ++u) {
+                    const u32 s = tid + (u32)(q0 + u) * THREADS;
+                    pe[u] = (q0 + u < E && s < m) ? (u32)sm.perm[s] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < UC; ++u) {
+                    const u32 s = tid + (u32)(q0 + u) * THREADS;
+                    if (q0 + u >= E || s >= m)
+                        continue;
+                    if constexpr (P16) {
+                        const u64 *r = recs + (u64)pe[u] * rw;
+                        if constexpr (RW == 2) {
+                            const uint4 x = *reinterpret_cast<const uint4 *>(r);  // the record, once
+                            const u64 w0v = ((u64)x.y << 32) | x.x, w1v = ((u64)x.w << 32) | x.z;
+                            const u64 lw = g.win.wl ? w1v : w0v, hw = g.win.wh ? w1v : w0v;
+                            const u32 d = digit_from(g, lw, hw, model);
+                            *reinterpret_cast<uint4 *>(dst + (item.begin + (u32)(sm.goff[d] + s)) * 2u) = x;
+                        } else {
+                            const u64 lw = r[g.win.wl];
+                            const u32 d = digit_from(g, lw, g.win.wh != g.win.wl ? r[g.win.wh] : lw, model);
+                            copy_record<RW>(dst + (item.begin + (u32)(sm.goff[d] + s)) * rw, r, rw);
+                        }
                     } else {
-                        const u64 lw = r[g.win.wl];
-                        const u32 d = digit_from(g, lw, g.win.wh != g.win.wl ? r[g.win.wh] : lw, model);
-                        copy_record<RW>(dst + (item.begin + (u32)(sm.goff[d] + s)) * rw, r, rw);
+                        copy_record<RW>(dst + (item.begin + (u32)(sm.goff[pe[u] >> 16] + s)) * rw,
+                                        recs + (u64)(pe[u] & 0xffffu) * rw, rw);
                     }
-                } else {
-                    copy_record<RW>(dst + (item.begin + (u32)(sm.goff[pe >> 16] + s)) * rw,
-                                    recs + (u64)(pe & 0xffffu) * rw, rw);
                 }
             }
             if (tid == 0)
