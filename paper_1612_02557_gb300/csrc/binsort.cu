@@ -3,27 +3,31 @@
 // with the next bin loading while the current one is sorted (Sec. 3.4-3.5:
 // small bins are finished where they fit, here in shared memory).
 //
-// One persistent CTA per SM takes the on-chip items in turn.  Its thread 0
-// starts a bulk asynchronous copy (TMA engine, one mbarrier per buffer) of the
-// next item into the second record buffer before the CTA sorts the current
-// one, so the SM keeps loading while it sorts.  An item whose records agree
-// on every key bit at or above `hi` is sorted in four steps:
+// One persistent CTA per SM takes the on-chip items in turn (CTA c takes items
+// c, c + G, c + 2G, ...).  Its thread 0 starts a bulk asynchronous copy (TMA
+// engine, one mbarrier per buffer) of the next item into the second record
+// buffer before the CTA sorts the current one, so the SM keeps loading while
+// it sorts.  An item whose records agree on every key bit at or above `hi` is
+// sorted in four steps:
 //   1. count: the code of a record is its key window [hi - cb, hi) (cb = 8 to
 //      13 bits, about two codes per record), counted in shared memory;
 //   2. exclusive prefix of the counters: the first slot of every code group;
 //   3. placement: every record takes the next slot of its group and leaves
-//      one 64-bit word there, (code, the 32 key bits below the code, its
+//      one 64-bit word there: (code, the 38 key bits below the code, its
 //      index in the item);
 //   4. final place: a record's rank inside its group comes from comparing
-//      those words (whole keys when the 32 bits tie, the index last, which
-//      keeps equal keys in input order); the record is copied from the buffer
-//      straight to its final place, which lies within its group's slots, so
-//      the warp's writes stay nearly contiguous.
-// When a code group holds more than BS_GMAX records, the highest key bit
+//      those words (warp shuffles inside a warp's 32 slots; whole keys when
+//      the packed bits tie; the index last, which keeps equal keys in input
+//      order); the record is copied from the buffer straight to its final
+//      place, which lies within its group's slots, so the warp's writes stay
+//      nearly contiguous.
+// When a code group holds more than BS_GSOFT records, the highest key bit
 // below `hi` that varies in the item is found (OR / AND of its key word) and
-// the count is taken again; an item that still has such groups (many equal
-// keys), is too big, or is a run of independent arrays goes to the general
-// on-chip kernel (blocksort.cu) through a second list.
+// the count is taken again at that bit.  An item that still has groups of
+// more than BS_GMAX records (many near-equal keys) is sorted by a bitonic
+// network on its slot words when they hold every key bit left; otherwise it,
+// a run of independent arrays or an item too big goes to the general on-chip
+// kernel (blocksort.cu) through a second list.
 #include "kernels.h"
 
 namespace raduls {
@@ -69,7 +73,6 @@ constexpr size_t binsort_smem_bytes(u32 rw)
 namespace {
 
 // The key bits of window x (1 to 63 bits wide) of a record.
-template <int RW>
 __device__ __forceinline__ u64 key_bits(const u64 *r, const Window &x)
 {
     const u64 lw = r[x.wl];
@@ -202,7 +205,7 @@ __device__ __forceinline__ bool bin_sort_item(BinSortSmem<THREADS, CAP> &sm, con
         // last's, so the bits above the highest window bit where those two
         // differ are shared by the whole run
         const Window pw = make_window(hi, run_w, key_words);
-        const u32 x = (u32)(key_bits<RW>(recs, pw) ^ key_bits<RW>(recs + (u64)(m - 1u) * RW, pw));
+        const u32 x = (u32)(key_bits(recs, pw) ^ key_bits(recs + (u64)(m - 1u) * RW, pw));
         hi = hi - run_w + (x ? 32u - (u32)__clz((int)x) : 0u);
     }
     if (m <= 1u || hi == 0u) {
@@ -232,7 +235,7 @@ __device__ __forceinline__ bool bin_sort_item(BinSortSmem<THREADS, CAP> &sm, con
         for (u32 k = 0; k < KPT; ++k) {
             const u32 e = tid + k * THREADS;
             if (recount && e < m) {
-                code[k] = (u32)key_bits<RW>(recs + (u64)e * RW, cw);
+                code[k] = (u32)key_bits(recs + (u64)e * RW, cw);
                 bump_code_cnt(sm.cnt, code[k]);
             }
         }
@@ -293,7 +296,7 @@ __device__ __forceinline__ bool bin_sort_item(BinSortSmem<THREADS, CAP> &sm, con
     const Window sw = make_window(sb ? lo : 64u, sb ? sb : 1u, key_words);
     const bool more = lo > sb;  // key bits below the packed ones
     auto word_of = [&](u32 c, u32 e) {
-        const u64 sec = sb ? key_bits<RW>(recs + (u64)e * RW, sw) : 0ull;
+        const u64 sec = sb ? key_bits(recs + (u64)e * RW, sw) : 0ull;
         return ((u64)c << BS_CODE_SHIFT) | (sec << BS_IDX_BITS) | (u64)e;
     };
     if (heavy) {
