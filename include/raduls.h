@@ -125,10 +125,11 @@ int raduls_sort_ex(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uin
  * two ranges must not overlap.  Both copies run on the library's own copy
  * stream, in chunks (the environment variable RADULS_COPY_STREAMS spreads
  * them over up to 8 streams; on GB300 one stream already moves about 200 GB/s
- * each way, the link's rate, and more streams were slower).  When the last
- * level of the sort is a mid-size level (and no record moves after it), that
- * level runs in 8 position windows and each window's records go back while
- * the next window is sorted (RADULS_HOST_WINDOWS=0 turns this off).  The
+ * each way, the link's rate, and more streams were slower).  The last step of the
+ * sort -- the streamed on-chip bin sort, or a mid-size level when no record
+ * moves after it -- runs in 8 position windows and each window's records go
+ * back while the next window is sorted (RADULS_HOST_WINDOWS=0 turns this
+ * off).  The
  * work is ordered on `stream` like every other call: h_in must stay unchanged
  * and h_out untouched until the stream has passed the call (synchronise it,
  * or call raduls_stream_status).  Pinned memory is much faster; pageable

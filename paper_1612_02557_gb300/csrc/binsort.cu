@@ -447,7 +447,8 @@ __device__ __forceinline__ u32 item_run_w(const WorkItem &it)
 template <int THREADS, int CAP, int RW>
 __global__ void __launch_bounds__(THREADS, 1)
 bin_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkItem *__restrict__ blocks,
-                WorkItem *__restrict__ fb, Counters *__restrict__ ctrs, u32 key_words, u64 fb_cap, u64 wait_ns)
+                WorkItem *__restrict__ fb, Counters *__restrict__ ctrs, u32 key_words, u64 fb_cap, u64 wait_ns,
+                const u32 *__restrict__ order, const u32 *__restrict__ wstart, u32 window)
 {
     using Sm = BinSortSmem<THREADS, CAP>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -458,7 +459,9 @@ bin_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkIte
     const u32 tid = threadIdx.x;
     if (cta_failed(ctrs))
         return;
-    const u64 n_items = ctrs->block;
+    // the whole on-chip list, or one position window of it
+    const u64 first = order ? wstart[window] : 0ull;
+    const u64 n_items = order ? wstart[window + 1] - first : ctrs->block;
     auto clear_counters = [&]() {
         uint4 *c4 = reinterpret_cast<uint4 *>(sm.cnt);
         for (u32 i = tid; i < BS_NW / 4u; i += THREADS)
@@ -474,7 +477,7 @@ bin_sort_kernel(u64 *__restrict__ in, const u64 *__restrict__ tmp, const WorkIte
     auto fetch = [&]() {
         nvalid = kidx < n_items;
         if (nvalid)
-            nd = blocks[kidx];
+            nd = blocks[order ? order[first + kidx] : kidx];
         kidx += gridDim.x;
     };
     // put the fetched item into buffer b: its load starts, or it goes to the
@@ -615,7 +618,8 @@ u32 binsort_rw_of(int var)
 }
 
 cudaError_t launch_bin_sort(int var, u64 *in, const u64 *tmp, const WorkItem *blocks, WorkItem *fb, Counters *ctrs,
-                            u32 key_words, u64 fb_cap, u64 wait_ns, cudaStream_t st)
+                            u32 key_words, u64 fb_cap, u64 wait_ns, cudaStream_t st, const u32 *order,
+                            const u32 *wstart, u32 window)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -627,8 +631,8 @@ cudaError_t launch_bin_sort(int var, u64 *in, const u64 *tmp, const WorkItem *bl
         cudaError_t e = prepare_binsort<T, CAP, RW>(&smem);                                                  \
         if (e != cudaSuccess)                                                                                \
             return e;                                                                                        \
-        bin_sort_kernel<T, CAP, RW><<<(u32)(sms > 0 ? sms : 1), T, smem, st>>>(in, tmp, blocks, fb, ctrs,     \
-                                                                              key_words, fb_cap, wait_ns);   \
+        bin_sort_kernel<T, CAP, RW><<<(u32)(sms > 0 ? sms : 1), T, smem, st>>>(                              \
+            in, tmp, blocks, fb, ctrs, key_words, fb_cap, wait_ns, order, wstart, window);                      \
         return cudaGetLastError();                                                                           \
     }
         BINSORT_VARIANTS(X)

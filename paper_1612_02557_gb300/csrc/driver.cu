@@ -919,7 +919,26 @@ int run_sort(Ctx &c, Work &wk, const SortJob &j, cudaStream_t st, Recorder *oute
         j.hout->copied = false;  // records still move after the last level
     if (!step_api) {
         TIMED(RADULS_K_COPY, launch_copy(s, j.in, j.tmp, L.copies, L.tile_copy, wk.ctrs, st));
-        if (s.bins_var >= 0) {
+        if (s.bins_var >= 0 && j.hout && !wk.h_ctrs->err && wk.h_ctrs->block > 0) {
+            // the last step of an end-to-end sort: the streamed bin sort runs
+            // in position windows (items grouped by their first record), and
+            // each window's records go back to the host while the next
+            // window is sorted; every record of window w is written by items
+            // that start at or before it, so it is final once w is done
+            const u32 nw = BUCKET_WINDOWS_MAX;
+            const u64 nb = wk.h_ctrs->block;
+            CK(ensure(wk.win, ((size_t)nb + nw + 1) * 4, false));
+            u32 *const order = (u32 *)wk.win.p, *const wstart = order + nb;
+            TIMED(RADULS_K_SETUP, launch_block_windows(L.blocks, wk.ctrs, j.n, nw, order, wstart, st));
+            for (u32 w = 0; w < nw; ++w) {
+                TIMED(RADULS_K_BLOCK, launch_bin_sort(s.bins_var, j.in, j.tmp, L.blocks, L.blocks_fb, wk.ctrs,
+                                                      s.key_words, L.caps.block, c.wait_ns, st, order, wstart, w));
+                TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks_fb, wk.ctrs, nullptr, st, true));
+                TIMED(RADULS_K_SETUP, launch_fb_window_reset(wk.ctrs, st));
+                CK(j.hout->copy(j.n * w / nw, w + 1 == nw ? j.n : j.n * (w + 1) / nw, w, st));
+            }
+            j.hout->copied = true;
+        } else if (s.bins_var >= 0) {
             TIMED(RADULS_K_BLOCK, launch_bin_sort(s.bins_var, j.in, j.tmp, L.blocks, L.blocks_fb, wk.ctrs,
                                                   s.key_words, L.caps.block, c.wait_ns, st));
             TIMED(RADULS_K_BLOCK, launch_block_sort(s, j.in, j.tmp, L.blocks_fb, wk.ctrs, nullptr, st, true));

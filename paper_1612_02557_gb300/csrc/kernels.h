@@ -50,8 +50,11 @@ cudaError_t launch_block_sort(const Shape &s, u64 *in, const u64 *tmp, const Wor
 int binsort_variant_for(u32 rw);
 u32 binsort_cap_of(int var);
 u32 binsort_rw_of(int var);
+// With `order` non-null, only window `window` of the on-chip list is taken:
+// items order[wstart[window]] .. order[wstart[window + 1] - 1].
 cudaError_t launch_bin_sort(int var, u64 *in, const u64 *tmp, const WorkItem *blocks, WorkItem *fb, Counters *ctrs,
-                            u32 key_words, u64 fb_cap, u64 wait_ns, cudaStream_t st);
+                            u32 key_words, u64 fb_cap, u64 wait_ns, cudaStream_t st, const u32 *order = nullptr,
+                            const u32 *wstart = nullptr, u32 window = 0);
 
 // The distribution pass over chunks (wide.cu): a histogram of every chunk's
 // digit window whose counts are chained along each bin's chunks by a
@@ -215,6 +218,11 @@ cudaError_t launch_keep_learned(Counters *ctrs, float ratio, cudaStream_t st);
 cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
                                   u32 *wstart, cudaStream_t st);
 cudaError_t launch_bucket_window_reset(Counters *ctrs, cudaStream_t st);
+// On-chip items grouped by position window (as launch_bucket_windows), and
+// the left-over list's counter moved past the items a window has finished.
+cudaError_t launch_block_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
+                                 u32 *wstart, cudaStream_t st);
+cudaError_t launch_fb_window_reset(Counters *ctrs, cudaStream_t st);
 cudaError_t launch_batched_init(const u64 *off, u32 n_segs, WorkItem *grid0, WorkItem *blocks, u32 *tile_hist,
                                 Counters *ctrs, Caps caps, u32 top, u32 cap_b, u32 tile_h, WorkItem *bucket0,
                                 u32 bucket_max, u64 *cell0, u32 leaf, u32 wmax, cudaStream_t st);

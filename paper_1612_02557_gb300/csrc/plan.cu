@@ -671,6 +671,47 @@ bucket_window_kernel(const WorkItem *__restrict__ items, const Counters *__restr
         order[atomicAdd(&pos[win_of(items[i].begin)], 1u)] = i;
 }
 
+// The same grouping for the on-chip items (end-to-end sorts whose last step
+// is the streamed bin sort): order[] lists indices into the on-chip list
+// window by window, wstart[w] is where window w starts.
+__global__ void __launch_bounds__(1024)
+block_window_kernel(const WorkItem *__restrict__ items, const Counters *__restrict__ ctrs, u64 n, u32 nw,
+                    u32 *__restrict__ order, u32 *__restrict__ wstart)
+{
+    __shared__ u32 cnt[BUCKET_WINDOWS_MAX], pos[BUCKET_WINDOWS_MAX];
+    const u64 m = ctrs->block;
+    const u32 tid = threadIdx.x;
+    auto win_of = [&](u64 b) {
+        const u64 w = n ? b * nw / n : 0;
+        return (u32)(w < nw ? w : nw - 1u);
+    };
+    if (tid < BUCKET_WINDOWS_MAX)
+        cnt[tid] = 0;
+    __syncthreads();
+    for (u64 i = tid; i < m; i += blockDim.x)
+        atomicAdd(&cnt[win_of(items[i].begin)], 1u);
+    __syncthreads();
+    if (tid == 0) {
+        u32 acc = 0;
+        for (u32 w = 0; w < nw; ++w) {
+            wstart[w] = acc;
+            pos[w] = acc;
+            acc += cnt[w];
+        }
+        wstart[nw] = acc;
+    }
+    __syncthreads();
+    for (u64 i = tid; i < m; i += blockDim.x)
+        order[atomicAdd(&pos[win_of(items[i].begin)], 1u)] = (u32)i;
+}
+
+// After a window's left-overs are sorted: every item on the left-over list so
+// far is done, the next window's general kernel starts after them.
+__global__ void fb_window_reset_kernel(Counters *c)
+{
+    c->fb_ctr = (u32)c->block_fb;
+}
+
 // Before the next window: the mid-size kernel's item counter and this level's
 // stable-split list start over (the previous window's split items are done).
 __global__ void bucket_window_reset_kernel(Counters *c)
@@ -686,6 +727,21 @@ cudaError_t launch_bucket_windows(const WorkItem *items, const Counters *ctrs, u
     if (nw < 1 || nw > BUCKET_WINDOWS_MAX)
         return cudaErrorInvalidValue;
     bucket_window_kernel<<<1, 1024, 0, st>>>(items, ctrs, n, nw, order, wstart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_windows(const WorkItem *items, const Counters *ctrs, u64 n, u32 nw, u32 *order,
+                                 u32 *wstart, cudaStream_t st)
+{
+    if (nw < 1 || nw > BUCKET_WINDOWS_MAX)
+        return cudaErrorInvalidValue;
+    block_window_kernel<<<1, 1024, 0, st>>>(items, ctrs, n, nw, order, wstart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fb_window_reset(Counters *ctrs, cudaStream_t st)
+{
+    fb_window_reset_kernel<<<1, 1, 0, st>>>(ctrs);
     return cudaGetLastError();
 }
 
