@@ -312,8 +312,10 @@ typedef struct {
  * undefined afterwards.  Synchronises `stream`; not for use inside a stream
  * capture.  `out` may be NULL.  Environment overrides still take precedence:
  * RADULS_SCATTER_VARIANT (one distribution shape for every level),
- * RADULS_WMAX (widest digit, 8..10), RADULS_LEAF (sub-bin size target),
- * RADULS_BLOCK_CAP, RADULS_BUCKET_MAX, RADULS_BIN_SORT (0/1). */
+ * RADULS_SCATTER8 / 9 / 10 (the shape of levels whose widest digit has that
+ * many bits), RADULS_WMAX (widest digit, 8..10), RADULS_LEAF (sub-bin size
+ * target), RADULS_BLOCK_CAP, RADULS_BUCKET_MAX (mid-size class, 0 = off),
+ * RADULS_BIN_SORT (0/1: the streamed on-chip sort), RADULS_BIN_VARIANT. */
 int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                     const uint64_t *d_seg_offsets, uint32_t n_segs, raduls_tuning *out, void *stream);
 

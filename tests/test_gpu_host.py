@@ -93,14 +93,17 @@ def test_bad_arguments_are_refused():
 
 
 @pytest.mark.parametrize("windows", ["1", "0"])
-def test_window_copy_back_on_and_off(oracle_mod, windows, monkeypatch):
-    """The last mid-size level copied back window by window (default) and the
-    whole array copied after the sort (RADULS_HOST_WINDOWS=0) give the same
-    bytes: 2^23 + 12,345 uniform records end in 256 mid-size bins (the
-    windowed case; windows do not fall on bin boundaries)."""
+@pytest.mark.parametrize("mid_size", ["0", "40960"])
+def test_window_copy_back_on_and_off(oracle_mod, windows, mid_size, monkeypatch):
+    """The last step copied back window by window (default) and the whole
+    array copied after the sort (RADULS_HOST_WINDOWS=0) give the same bytes:
+    2^23 + 12,345 uniform records end in runs of small sub-bins for the
+    streamed on-chip sort (the default) or, with the mid-size class on, in
+    256 mid-size bins; windows do not fall on item boundaries."""
     import torch
     p = lib()
     monkeypatch.setenv("RADULS_HOST_WINDOWS", windows)
+    monkeypatch.setenv("RADULS_BUCKET_MAX", mid_size)
     n = (1 << 23) + 12_345
     recs = datagen.WORKLOADS["uniform16"](n)
     h_in = torch.from_numpy(recs.view(np.int64)).pin_memory()
