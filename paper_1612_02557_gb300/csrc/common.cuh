@@ -633,6 +633,23 @@ __device__ __forceinline__ u32 peers_of(u32 d)
     return peers;
 }
 
+// The same for digits of `bits` bits, bits <= NB (the votes of the bits above
+// are skipped; `bits` is the same in every lane).
+template <int NB>
+__device__ __forceinline__ u32 peers_of_bits(u32 d, u32 bits)
+{
+    u32 peers = FULL_MASK;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        if ((u32)b < bits) {
+            const bool bit = (d >> b) & 1u;
+            const u32 bal = __ballot_sync(FULL_MASK, bit);
+            peers &= bit ? bal : ~bal;
+        }
+    }
+    return peers;
+}
+
 // Phase 1 of a stable block ranking (used by the distribution pass and the
 // on-chip sort).  Elements are laid out warp-contiguously: warp w owns
 // elements [w*32*K, (w+1)*32*K), lane l holds element w*32*K + k*32 + l in slot

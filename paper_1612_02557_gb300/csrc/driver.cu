@@ -39,6 +39,10 @@ bool scatter_variant_fits(int v, u32 rw)
     case 9:
     case 10:
     case 11:
+    case 16:
+    case 17:
+    case 18:
+    case 19:
         return rw == 2;
     case 6:
     case 12:

@@ -22,13 +22,14 @@
 //     CTA ever waits for another.  It streams the chunk through shared memory
 //     in tiles (bulk asynchronous copies; with two buffers the next tile loads
 //     while this one is ranked), ranks each tile's records stably by digit
-//     (one match instruction per record finds its peers in the warp, per-warp
+//     (one vote per digit bit finds a record's peers in the warp, per-warp
 //     counters give ranks in element order), regroups them so that every
 //     digit's records leave as one contiguous run (the role of the paper's
 //     write-combining buffers, Sec. 2, Sec. 3.2), and advances the cursors.
 // A digit is a window of up to 10 key bits (the Window of common.cuh), or the
 // learned model's bucket, so one pass can split a bin 1,024 ways; the width
 // of each bin's digit is picked when the bin is planned.
+#include <cstddef>
 #include <type_traits>
 
 #include "kernels.h"
@@ -267,10 +268,16 @@ template <int THREADS, int E, int KM, bool P16>
 struct WScatterSmem {
     static constexpr int NW = THREADS / 32;
     using PermT = typename std::conditional<P16, unsigned short, u32>::type;
+    // the rank step's byte tags (one per warp and value) take the place of
+    // goff, tstart and perm, which are written only after it, plus tag_pad
+    static constexpr size_t TAG_NEED = (size_t)NW * KM;
+    static constexpr size_t TAG_HAVE = 8u * (size_t)KM + sizeof(PermT) * THREADS * E;
+    static constexpr size_t TAG_PAD = TAG_NEED > TAG_HAVE ? TAG_NEED - TAG_HAVE : 0;
     unsigned short cnt[NW][KM];       // per warp: records of each value in the tile, then its offsets
     u32 goff[KM];                     // position of sorted slot 0's value run, per value, from the bin's start
     u32 tstart[KM];                   // first sorted slot of every value in the tile
     PermT perm[THREADS * E];          // sorted slot -> element (| value << 16 unless P16)
+    unsigned char tag_pad[TAG_PAD ? TAG_PAD : 1];
     u32 wsum[NW];
     u64 bar[2];                       // bulk-copy barriers of the two record buffers
     WorkItem item;
@@ -293,10 +300,30 @@ constexpr size_t wscatter_smem_bytes(u32 rw)
 }
 
 
+// How a warp finds the lanes that share a record's digit (its peers).  By
+// default through byte tags in shared memory: every lane writes its lane
+// number at its digit's tag and reads the tag back, and a lane that reads
+// another lane's number (a loser) shares its digit, so a warp whose 32 digits
+// all differ -- the common case for digits of 9 or 10 bits -- needs one vote;
+// a few losers are resolved with shuffles, more with one vote per digit bit.
+// WS_VOTE always takes the votes per digit bit, WS_MATCH one match
+// instruction per element.  Measured on 2^31 x 16 B (passes of 10- and 9-bit
+// digits): match 47.1 ms, votes 40.5-42.4 ms, tags 36.5 ms.
+constexpr int WS_MATCH = 1, WS_VOTE = 2;
+
+template <int KM>
+constexpr int log2_of()
+{
+    int b = 0;
+    while ((1 << b) < KM)
+        ++b;
+    return b;
+}
+
 // KM: the most digit values a launch handles (the widest digit of its level);
 // NB: record buffers -- 2, the next tile loads while this one is ranked;
 // 1, a smaller footprint that lets two CTAs share an SM instead.
-template <int THREADS, int E, int RW, int KM, int NB>
+template <int THREADS, int E, int RW, int KM, int NB, int FL = 0>
 __global__ void __launch_bounds__(THREADS, NB == 1 ? 2 : 1)
 wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__restrict__ items,
                 const u32 *__restrict__ tile_item, const u64 *__restrict__ cell_off, const u64 *__restrict__ status,
@@ -434,8 +461,8 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                 continue;
             }
             // Stable rank of the tile's elements by value: each warp ranks its
-            // own elements in element order (peers of a value found with one
-            // match instruction, counts in the warp's own row), then the
+            // own elements in element order (peers of a value found by one
+            // vote per digit bit, counts in the warp's own row), then the
             // warps' counts become per-warp offsets and the tile's totals an
             // exclusive prefix.  Padding elements (past m) take the largest
             // value and come last, so they shift no real element.
@@ -452,6 +479,11 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
             }
             __syncwarp();
             const u32 lt = lanemask_lt();
+            // this warp's tags, one per digit value (in goff .. tag_pad)
+            constexpr bool TAGS = (FL & (WS_MATCH | WS_VOTE)) == 0;
+            static_assert(offsetof(Sm, tag_pad) + sizeof(sm.tag_pad) - offsetof(Sm, goff) >= Sm::TAG_NEED,
+                          "the tags fit the borrowed arrays");
+            unsigned char *const tag = reinterpret_cast<unsigned char *>(sm.goff) + (size_t)w * KM;
             u32 dr[E];
 #pragma unroll
             for (int q = 0; q < E; ++q) {
@@ -462,7 +494,35 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                     const u64 lw = r[g.win.wl];
                     d = digit_from(g, lw, g.win.wh != g.win.wl ? r[g.win.wh] : lw, model);
                 }
-                const u32 peers = __match_any_sync(FULL_MASK, d);
+                u32 peers;
+                if constexpr ((FL & WS_MATCH) != 0) {
+                    peers = __match_any_sync(FULL_MASK, d);
+                } else if constexpr (TAGS) {
+                    // the last writer of a shared tag is read by its peers
+                    // (the losers); a loser tells its winner, and every lane
+                    // takes the winner's set.  The warp-wide syncs of the
+                    // counter update below order these reads before the
+                    // next element's writes.
+                    tag[d] = (unsigned char)lane;
+                    __syncwarp();
+                    const u32 t1 = tag[d];
+                    const u32 losers = __ballot_sync(FULL_MASK, t1 != lane);
+                    if (losers == 0u) {
+                        peers = 1u << lane;
+                    } else if (__popc(losers) <= 3) {
+                        u32 wm = 0;
+                        for (u32 rest = losers; rest != 0u; rest &= rest - 1u) {
+                            const u32 l = (u32)__ffs((int)rest) - 1u;
+                            if (__shfl_sync(FULL_MASK, t1, l) == lane)
+                                wm |= 1u << l;
+                        }
+                        peers = __shfl_sync(FULL_MASK, wm, t1) | (1u << t1);
+                    } else {
+                        peers = peers_of_bits<log2_of<KM>()>(d, g.win.w);
+                    }
+                } else {
+                    peers = peers_of_bits<log2_of<KM>()>(d, g.win.w);
+                }
                 const u32 prev = sm.cnt[w][d];
                 __syncwarp();
                 if ((peers & lt) == 0)  // the lowest lane of the peer group bumps the count
@@ -634,30 +694,35 @@ constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
 // distribution variants: {id, threads, E, RW, KM, NB}; 5-15 fit two CTAs on
 // an SM (5-7 take digits of at most 8 bits, 9, 12 and 14 of 9 bits; those of
 // 10 bits keep a 16-bit permutation: 8 with smaller tiles, 10 with fewer,
-// longer warps, 11, 13 and 15 the tile of the 8-bit shape of their width)
-#define WSCATTER_VARIANTS(X)            \
-    X(0, 512, 8, 1, KMAX, 2)            \
-    X(1, 512, 8, 2, KMAX, 2)            \
-    X(2, 512, 4, 4, KMAX, 2)            \
-    X(3, 512, 2, 0, KMAX, 2)            \
-    X(4, 256, 1, 0, KMAX, 2)            \
-    X(5, 512, 8, 2, 256, 1)             \
-    X(6, 512, 8, 1, 256, 1)             \
-    X(7, 512, 4, 4, 256, 1)             \
-    X(8, 512, 4, 2, KMAX, 1)            \
-    X(9, 512, 8, 2, 512, 1)             \
-    X(10, 256, 16, 2, KMAX, 1)          \
-    X(11, 512, 8, 2, KMAX, 1)           \
-    X(12, 512, 8, 1, 512, 1)            \
-    X(13, 512, 8, 1, KMAX, 1)           \
-    X(14, 512, 4, 4, 512, 1)            \
-    X(15, 512, 4, 4, KMAX, 1)
+// longer warps, 11, 13 and 15 the tile of the 8-bit shape of their width;
+// 16 and 17 are 11 and 9 with match-instruction ranks, 18 and 19 with votes)
+#define WSCATTER_VARIANTS(X)             \
+    X(0, 512, 8, 1, KMAX, 2, 0)          \
+    X(1, 512, 8, 2, KMAX, 2, 0)          \
+    X(2, 512, 4, 4, KMAX, 2, 0)          \
+    X(3, 512, 2, 0, KMAX, 2, 0)          \
+    X(4, 256, 1, 0, KMAX, 2, 0)          \
+    X(5, 512, 8, 2, 256, 1, 0)           \
+    X(6, 512, 8, 1, 256, 1, 0)           \
+    X(7, 512, 4, 4, 256, 1, 0)           \
+    X(8, 512, 4, 2, KMAX, 1, 0)          \
+    X(9, 512, 8, 2, 512, 1, 0)           \
+    X(10, 256, 16, 2, KMAX, 1, 0)        \
+    X(11, 512, 8, 2, KMAX, 1, 0)         \
+    X(12, 512, 8, 1, 512, 1, 0)          \
+    X(13, 512, 8, 1, KMAX, 1, 0)         \
+    X(14, 512, 4, 4, 512, 1, 0)          \
+    X(15, 512, 4, 4, KMAX, 1, 0)         \
+    X(16, 512, 8, 2, KMAX, 1, WS_MATCH)  \
+    X(17, 512, 8, 2, 512, 1, WS_MATCH)   \
+    X(18, 512, 8, 2, KMAX, 1, WS_VOTE)   \
+    X(19, 512, 8, 2, 512, 1, WS_VOTE)
 
-template <int THREADS, int E, int RW, int KM, int NB>
+template <int THREADS, int E, int RW, int KM, int NB, int FL>
 cudaError_t prepare_wscatter(u32 rw, size_t *smem)
 {
     *smem = wscatter_smem_bytes<THREADS, E, KM, NB>(rw);
-    return cudaFuncSetAttribute(wscatter_kernel<THREADS, E, RW, KM, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(wscatter_kernel<THREADS, E, RW, KM, NB, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)*smem);
 }
 
@@ -674,7 +739,7 @@ u32 sm_count()
 u32 wscatter_tile_of(int var)
 {
     switch (var) {
-#define X(v, T, E, RW, KM, NB) \
+#define X(v, T, E, RW, KM, NB, FL) \
     case v:                    \
         return T * E;
         WSCATTER_VARIANTS(X)
@@ -686,7 +751,7 @@ u32 wscatter_tile_of(int var)
 u32 wscatter_kmax_of(int var)
 {
     switch (var) {
-#define X(v, T, E, RW, KM, NB) \
+#define X(v, T, E, RW, KM, NB, FL) \
     case v:                    \
         return KM;
         WSCATTER_VARIANTS(X)
@@ -698,12 +763,12 @@ u32 wscatter_kmax_of(int var)
 u32 wscatter_grid(const Shape &s)
 {
     switch (s.scat_var) {
-#define X(v, T, E, RW, KM, NB)                                                                            \
+#define X(v, T, E, RW, KM, NB, FL)                                                                            \
     case v: {                                                                                             \
         size_t smem = 0;                                                                                  \
-        prepare_wscatter<T, E, RW, KM, NB>(s.rw, &smem);                                                  \
+        prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                                  \
         int per_sm = 0;                                                                                   \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wscatter_kernel<T, E, RW, KM, NB>, T, smem); \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wscatter_kernel<T, E, RW, KM, NB, FL>, T, smem); \
         return sm_count() * (u32)(per_sm < 1 ? 1 : per_sm);                                               \
     }
         WSCATTER_VARIANTS(X)
@@ -745,13 +810,13 @@ cudaError_t launch_wscatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *i
 {
     const u32 grid = wscatter_grid(s);
     switch (s.scat_var) {
-#define X(v, T, E, RW, KM, NB)                                                                              \
+#define X(v, T, E, RW, KM, NB, FL)                                                                              \
     case v: {                                                                                               \
         size_t smem = 0;                                                                                    \
-        cudaError_t e = prepare_wscatter<T, E, RW, KM, NB>(s.rw, &smem);                                    \
+        cudaError_t e = prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                    \
         if (e != cudaSuccess)                                                                               \
             return e;                                                                                       \
-        wscatter_kernel<T, E, RW, KM, NB><<<grid, T, smem, st>>>(in, tmp, items, tile_item, cell_off, status, \
+        wscatter_kernel<T, E, RW, KM, NB, FL><<<grid, T, smem, st>>>(in, tmp, items, tile_item, cell_off, status, \
                                                                  ctrs, s.tile_h, s.rw, s.key_words, model,    \
                                                                  wait_ns);                                    \
         return cudaGetLastError();                                                                          \

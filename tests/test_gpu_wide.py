@@ -87,3 +87,32 @@ def test_many_chunks_and_skewed_bins(oracle_mod):
         with _env(RADULS_WMAX=wmax):
             got = gpu_sort(recs, 8)
         np.testing.assert_array_equal(got, oracle_mod.sort(recs, 8, threads=8), err_msg=f"wmax {wmax}")
+
+
+@pytest.mark.parametrize("rec_bytes,v9,v10", [(16, 9, 11), (16, 17, 16), (16, 19, 18), (32, 14, 15), (8, 12, 13)])
+@pytest.mark.parametrize("case", ["uniform", "few_values", "two_word_keys", "ragged"])
+def test_scatter_shapes_of_9_and_10_bit_digits(oracle_mod, rec_bytes, v9, v10, case):
+    # every two-CTA shape of 9- and 10-bit digits gives the same bytes, with
+    # tag ranks (the default), match ranks (16-byte shapes 17 and 16) or vote
+    # ranks (19 and 18): partial last tiles, values shared by many records
+    # (the tags' vote fallback), windows in the second key word
+    n, key_bytes, alphabet = 1_000_003, 8, None
+    if case == "few_values":
+        alphabet = 7
+    elif case == "two_word_keys":
+        if rec_bytes == 8:
+            pytest.skip("8-byte records hold one key word")
+        key_bytes = 16
+    elif case == "ragged":
+        n = 4096 * 37 + 1
+    recs = datagen.random_records(n, rec_bytes, key_bytes, v10 * 1000 + len(case), alphabet=alphabet)
+    if case == "two_word_keys":
+        recs[:, 0] &= np.uint64(0xFFFF)  # the top key bits tie: later windows reach into word 1
+    want = oracle_mod.sort(recs, key_bytes, threads=8)
+    # 8-byte records take one shape for every level (no per-width shapes)
+    shapes = ([{"RADULS_SCATTER_VARIANT": v9}, {"RADULS_SCATTER_VARIANT": v10}] if rec_bytes == 8 else
+              [{"RADULS_SCATTER9": v9, "RADULS_SCATTER10": v10}])
+    for leaf in (300, 4096):
+        for sh in shapes:
+            with _env(RADULS_LEAF=leaf, **sh):
+                np.testing.assert_array_equal(gpu_sort(recs, key_bytes), want)
