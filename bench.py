@@ -89,7 +89,7 @@ WORKLOADS = {
 # 16-byte records.  A class missing here has no capture of its current code.
 DRAM_BYTES_PER_RECORD = {
     # wscatter_kernel, a 2^27-record sort split 10 bits (variant 11) then 9 bits (variant 9)
-    "scatter": (2.623124e9 + 2.481391e9 + 2.299407e9 + 2.214017e9) / 2 / 2 ** 27,
+    "scatter": (2.605462e9 + 2.451761e9 + 2.291758e9 + 2.199927e9) / 2 / 2 ** 27,
     # bin_sort_kernel, 2^27 records in ~2,048-record bins
     "block": (2.151157e9 + 2.090265e9) / 2 ** 27,
     # bucket_kernel, 10^7 records in 256 mid-size bins

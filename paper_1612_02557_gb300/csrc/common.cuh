@@ -525,6 +525,30 @@ __device__ __forceinline__ u32 digit_of_word(u64 w, u32 shift)
     return (u32)(w >> shift) & 0xffu;
 }
 
+// L2 eviction policies (createpolicy): records read or written for the last
+// time leave L2 first; data that is read or completed again soon stays.
+__device__ __forceinline__ u64 l2_evict_first()
+{
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ u64 l2_evict_last()
+{
+    u64 p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// A 16-byte store to global memory under L2 policy pol.
+__device__ __forceinline__ void st_global_v4_hint(void *g, const uint4 &v, u64 pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(g), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // Copy one record of rw words (RW > 0: compile-time width) from shared to
 // global memory.  16-byte vectors are used when both sides allow it.
 template <int RW>

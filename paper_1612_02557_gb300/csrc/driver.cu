@@ -43,6 +43,8 @@ bool scatter_variant_fits(int v, u32 rw)
     case 17:
     case 18:
     case 19:
+    case 20:
+    case 21:
         return rw == 2;
     case 6:
     case 12:

@@ -59,22 +59,6 @@ __device__ __forceinline__ void discard_range(const void *lo, const void *hi)
         discard_l2_line((const void *)x);
 }
 
-// L2 eviction policies (createpolicy): records read or written for the last
-// time leave L2 first; the private scratch copy stays until it is consumed.
-__device__ __forceinline__ u64 l2_evict_first()
-{
-    u64 p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ u64 l2_evict_last()
-{
-    u64 p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
 template <int RW>
 __device__ __forceinline__ void load_rec_hint(u64 (&r)[RW], const u64 *g, u64 pol)
 {

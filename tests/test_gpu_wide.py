@@ -89,13 +89,14 @@ def test_many_chunks_and_skewed_bins(oracle_mod):
         np.testing.assert_array_equal(got, oracle_mod.sort(recs, 8, threads=8), err_msg=f"wmax {wmax}")
 
 
-@pytest.mark.parametrize("rec_bytes,v9,v10", [(16, 9, 11), (16, 17, 16), (16, 19, 18), (32, 14, 15), (8, 12, 13)])
+@pytest.mark.parametrize("rec_bytes,v9,v10", [(16, 9, 11), (16, 17, 16), (16, 19, 18), (16, 21, 20), (32, 14, 15), (8, 12, 13)])
 @pytest.mark.parametrize("case", ["uniform", "few_values", "two_word_keys", "ragged"])
 def test_scatter_shapes_of_9_and_10_bit_digits(oracle_mod, rec_bytes, v9, v10, case):
     # every two-CTA shape of 9- and 10-bit digits gives the same bytes, with
     # tag ranks (the default), match ranks (16-byte shapes 17 and 16) or vote
-    # ranks (19 and 18): partial last tiles, values shared by many records
-    # (the tags' vote fallback), windows in the second key word
+    # ranks (19 and 18), evict-last stores (the default) or plain ones (21 and
+    # 20): partial last tiles, values shared by many records (the tags' vote
+    # fallback), windows in the second key word
     n, key_bytes, alphabet = 1_000_003, 8, None
     if case == "few_values":
         alphabet = 7
