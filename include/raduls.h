@@ -284,7 +284,7 @@ int raduls_histogram_static(const void *in, uint64_t n_recs, uint32_t rec_bytes,
 
 /* Settings picked by raduls_autotune. */
 typedef struct {
-    int32_t  scatter_variant;  /* distribution kernel shape (threads x records per thread) */
+    int32_t  scatter_variant;  /* distribution kernel shape (threads x records per thread, widest digit) */
     uint32_t scatter_tile;     /* records per distribution tile of that shape */
     uint32_t block_cap;        /* largest bin (or run of small bins / arrays) sorted by one CTA on chip */
     uint32_t bucket_max;       /* largest mid-size bin sorted by one CTA through L2 (0: class off) */
@@ -299,10 +299,11 @@ typedef struct {
  * (the paper has no counterpart; its scheduling constants, Sec. 3.2-3.5, are
  * CPU-specific).  Fills `in` with seeded uniform records (SplitMix64 words),
  * sorts them once per candidate setting -- every distribution tile shape
- * that fits the record width, the widest digit at 8, 9 and 10 bits, two
- * sub-bin size targets, the on-chip class at its full and half capacity, the
- * streamed on-chip bin sort on and off, the mid-size class off, at half and
- * at full size -- with `tmp` as scratch, times each with CUDA events (best of
+ * that fits the record width (shapes 0-15; 16-21 differ from 11 and 9 only
+ * in how warps rank or store, kept for comparison), the widest digit at 8, 9
+ * and 10 bits, two sub-bin size targets, the on-chip class at its full and
+ * half capacity, the streamed on-chip bin sort on and off, the mid-size
+ * class off, at half and at full size -- with `tmp` as scratch, times each with CUDA events (best of
  * two), and keeps the fastest for later calls on this device with this record
  * width (candidates go from the default shape outward, and the winner must
  * beat the default by more than 1% in a final alternating re-timing, so
