@@ -303,19 +303,20 @@ typedef struct {
  * in how warps rank or store, kept for comparison), the widest digit at 8, 9
  * and 10 bits, two sub-bin size targets, the on-chip class at its full and
  * half capacity, the streamed on-chip bin sort on and off, the mid-size
- * class off, at half and at full size -- with `tmp` as scratch, times each with CUDA events (best of
- * two), and keeps the fastest for later calls on this device with this record
- * width (candidates go from the default shape outward, and the winner must
- * beat the default by more than 1% in a final alternating re-timing, so
- * timing noise never trades the default for a setting that only uniform keys
- * tolerate): plain sorts when d_seg_offsets is NULL, batched sorts (with those
- * offsets) otherwise.  `in` and `tmp` hold n_recs records; their contents are
- * undefined afterwards.  Synchronises `stream`; not for use inside a stream
- * capture.  `out` may be NULL.  Environment overrides still take precedence:
- * RADULS_SCATTER_VARIANT (one distribution shape for every level),
- * RADULS_SCATTER8 / 9 / 10 (the shape of levels whose widest digit has that
- * many bits), RADULS_WMAX (widest digit, 8..10), RADULS_LEAF (sub-bin size
- * target), RADULS_BLOCK_CAP, RADULS_BUCKET_MAX (mid-size class, 0 = off),
+ * class off, at half and at full size -- with `tmp` as scratch, times each
+ * with CUDA events (best of two), and keeps the fastest for later calls on
+ * this device with this record width (candidates go from the default shape
+ * outward, and the winner must beat the default by more than 1% in a final
+ * alternating re-timing, so timing noise never trades the default for a
+ * setting that only uniform keys tolerate): plain sorts when d_seg_offsets
+ * is NULL, batched sorts (with those offsets) otherwise.  `in` and `tmp`
+ * hold n_recs records; their contents are undefined afterwards.
+ * Synchronises `stream`; not for use inside a stream capture.  `out` may be
+ * NULL.  Environment overrides still take precedence: RADULS_SCATTER_VARIANT
+ * (one distribution shape for every level), RADULS_SCATTER8 / 9 / 10 (the
+ * shape of levels whose widest digit has that many bits), RADULS_WMAX
+ * (widest digit, 8..10), RADULS_LEAF (sub-bin size target),
+ * RADULS_BLOCK_CAP, RADULS_BUCKET_MAX (mid-size class, 0 = off),
  * RADULS_BIN_SORT (0/1: the streamed on-chip sort), RADULS_BIN_VARIANT. */
 int raduls_autotune(void *in, void *tmp, uint64_t n_recs, uint32_t rec_bytes, uint32_t key_bytes,
                     const uint64_t *d_seg_offsets, uint32_t n_segs, raduls_tuning *out, void *stream);
