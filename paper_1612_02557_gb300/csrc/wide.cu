@@ -22,10 +22,11 @@
 //     CTA ever waits for another.  It streams the chunk through shared memory
 //     in tiles (bulk asynchronous copies; with two buffers the next tile loads
 //     while this one is ranked), ranks each tile's records stably by digit
-//     (one vote per digit bit finds a record's peers in the warp, per-warp
-//     counters give ranks in element order), regroups them so that every
-//     digit's records leave as one contiguous run (the role of the paper's
-//     write-combining buffers, Sec. 2, Sec. 3.2), and advances the cursors.
+//     (byte tags in shared memory and one vote find a record's peers in the
+//     warp, per-warp counters give ranks in element order), regroups them so
+//     that every digit's records leave as one contiguous run (the role of the
+//     paper's write-combining buffers, Sec. 2, Sec. 3.2), and advances the
+//     cursors.
 // A digit is a window of up to 10 key bits (the Window of common.cuh), or the
 // learned model's bucket, so one pass can split a bin 1,024 ways; the width
 // of each bin's digit is picked when the bin is planned.
@@ -465,8 +466,8 @@ wscatter_kernel(u64 *__restrict__ in, u64 *__restrict__ tmp, const WorkItem *__r
                 continue;
             }
             // Stable rank of the tile's elements by value: each warp ranks its
-            // own elements in element order (peers of a value found by one
-            // vote per digit bit, counts in the warp's own row), then the
+            // own elements in element order (peers of a value found through
+            // byte tags, counts in the warp's own row), then the
             // warps' counts become per-warp offsets and the tile's totals an
             // exclusive prefix.  Padding elements (past m) take the largest
             // value and come last, so they shift no real element.
@@ -703,7 +704,7 @@ namespace {
 
 constexpr int WHIST_THREADS = 512, WHIST_UNROLL = 8;
 
-// distribution variants: {id, threads, E, RW, KM, NB}; 5-15 fit two CTAs on
+// distribution variants: {id, threads, E, RW, KM, NB, FL}; 5-21 fit two CTAs on
 // an SM (5-7 take digits of at most 8 bits, 9, 12 and 14 of 9 bits; those of
 // 10 bits keep a 16-bit permutation: 8 with smaller tiles, 10 with fewer,
 // longer warps, 11, 13 and 15 the tile of the 8-bit shape of their width;
@@ -755,7 +756,7 @@ u32 wscatter_tile_of(int var)
 {
     switch (var) {
 #define X(v, T, E, RW, KM, NB, FL) \
-    case v:                    \
+    case v:                        \
         return T * E;
         WSCATTER_VARIANTS(X)
 #undef X
@@ -767,7 +768,7 @@ u32 wscatter_kmax_of(int var)
 {
     switch (var) {
 #define X(v, T, E, RW, KM, NB, FL) \
-    case v:                    \
+    case v:                        \
         return KM;
         WSCATTER_VARIANTS(X)
 #undef X
@@ -778,13 +779,13 @@ u32 wscatter_kmax_of(int var)
 u32 wscatter_grid(const Shape &s)
 {
     switch (s.scat_var) {
-#define X(v, T, E, RW, KM, NB, FL)                                                                            \
-    case v: {                                                                                             \
-        size_t smem = 0;                                                                                  \
-        prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                                  \
-        int per_sm = 0;                                                                                   \
+#define X(v, T, E, RW, KM, NB, FL)                                                                              \
+    case v: {                                                                                                   \
+        size_t smem = 0;                                                                                        \
+        prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                                    \
+        int per_sm = 0;                                                                                         \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wscatter_kernel<T, E, RW, KM, NB, FL>, T, smem); \
-        return sm_count() * (u32)(per_sm < 1 ? 1 : per_sm);                                               \
+        return sm_count() * (u32)(per_sm < 1 ? 1 : per_sm);                                                     \
     }
         WSCATTER_VARIANTS(X)
 #undef X
@@ -825,16 +826,16 @@ cudaError_t launch_wscatter(const Shape &s, u64 *in, u64 *tmp, const WorkItem *i
 {
     const u32 grid = wscatter_grid(s);
     switch (s.scat_var) {
-#define X(v, T, E, RW, KM, NB, FL)                                                                              \
-    case v: {                                                                                               \
-        size_t smem = 0;                                                                                    \
-        cudaError_t e = prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                    \
-        if (e != cudaSuccess)                                                                               \
-            return e;                                                                                       \
+#define X(v, T, E, RW, KM, NB, FL)                                                                                \
+    case v: {                                                                                                     \
+        size_t smem = 0;                                                                                          \
+        cudaError_t e = prepare_wscatter<T, E, RW, KM, NB, FL>(s.rw, &smem);                                      \
+        if (e != cudaSuccess)                                                                                     \
+            return e;                                                                                             \
         wscatter_kernel<T, E, RW, KM, NB, FL><<<grid, T, smem, st>>>(in, tmp, items, tile_item, cell_off, status, \
-                                                                 ctrs, s.tile_h, s.rw, s.key_words, model,    \
-                                                                 wait_ns);                                    \
-        return cudaGetLastError();                                                                          \
+                                                                 ctrs, s.tile_h, s.rw, s.key_words, model,        \
+                                                                 wait_ns);                                        \
+        return cudaGetLastError();                                                                                \
     }
         WSCATTER_VARIANTS(X)
 #undef X
